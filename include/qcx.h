@@ -1,0 +1,208 @@
+/*
+ * qcx.h -- C ABI of libqcx, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of all-electron RPA screening with local-field
+ * effects (arXiv 2603.12326, "QCDark2").
+ *
+ * The path, in the paper's order:
+ *   pair densities  rho_vck(q+G) = <c,k+q| e^{i(q+G).r} |v,k>      (Eq. (RPA) numerator, Sec. II.D, III)
+ *   chi0_GG'(q,w)   = 2/(N_k V) sum_t W_t(w) rho_t(G)^* rho_t(G')   (Eq. (RPA))
+ *   eps_GG'         = delta_GG' - v^1/2(q+G) chi0_GG' v^1/2(q+G')    (Eq. (RPA))
+ *   [eps^-1]_GG     -> eps(w, q+G) = 1/[eps^-1]_GG                   (Eq. (eps_LFE))
+ *   eps_GG          -> eps^noLFE(w, q+G)                             (Eq. (eps_noLFE))
+ *   L = Im[-1/eps]  and the halo scattering rate / recoil spectrum  (Eqs. (dynamic_structure_factor),
+ *                                                                      (cross_section), (excitation_rate))
+ * with W_t(w) = 1/(w - dE_t + i eta) - 1/(w + dE_t + i eta) (T = 0 occupations,
+ * retarded broadening) and v^1/2(k) = sqrt(4 pi)/|k|.
+ *
+ * Units: Hartree atomic units (bohr, Hartree) at every entry point except
+ * qcx_halo_params, which uses the units named in its fields.
+ *
+ * Conventions for every entry point
+ *  - Inputs are copied before the call returns; the caller keeps ownership.
+ *  - Array arguments may be host or device pointers; residency is detected
+ *    with cudaPointerGetAttributes.  Device pointers must belong to the
+ *    context's device.
+ *  - Outputs are caller-owned.  A NULL output pointer means "not wanted".
+ *    When every output of a call is in device memory the call is
+ *    asynchronous on the context's stream; a host output makes the call
+ *    synchronise before returning.
+ *  - Complex numbers are qcx_c64 {re, im} (two doubles, interleaved).
+ *  - Errors: every call returns a qcx_status; on failure the context keeps
+ *    a message (qcx_last_error) and stays usable.  No C++ exception crosses
+ *    the ABI.  Calls made out of order return QCX_ERR_STATE.
+ *  - One context is used by one host thread at a time.
+ *  - Index t of a transition is (k * n_v + v) * n_c + c.
+ *  - G vectors are integer coefficients on the reciprocal basis b_1, b_2,
+ *    b_3 (a_i . b_j = 2 pi delta_ij).
+ */
+#ifndef QCX_H
+#define QCX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qcx_ctx qcx_ctx;
+
+typedef enum {
+    QCX_OK = 0,
+    QCX_ERR_ARG = 1,            /* invalid argument (size, NULL, range)                 */
+    QCX_ERR_ALLOC = 2,          /* device or host allocation failed                     */
+    QCX_ERR_CUDA = 3,           /* a CUDA runtime/driver call failed                    */
+    QCX_ERR_SINGULAR = 4,       /* a dielectric matrix had a zero pivot                 */
+    QCX_ERR_NOT_CONVERGED = 5,  /* refinement did not reach its residual bound          */
+    QCX_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up                   */
+    QCX_ERR_STATE = 7,          /* call made before the state it needs exists           */
+    QCX_ERR_UNSUPPORTED = 8     /* input outside what this build handles (see message)  */
+} qcx_status;
+
+typedef enum {
+    QCX_FP64 = 0,   /* plain FP64 throughout                                                    */
+    QCX_MIXED = 1   /* FP32 pair densities, chi0 as split-BF16 (hi*hi + hi*lo + lo*hi) tcgen05
+                       products with FP32 accumulation, FP32 Gauss-Jordan inverse with an FP64
+                       residual correction; dE and W in FP64                                       */
+} qcx_precision;
+
+typedef struct { double re, im; } qcx_c64;
+
+/* Halo and detector parameters of the nonrelativistic rate (Sec. II.B, IV.B
+ * footnote; Appendix A).  m_med_eV < 0 selects the heavy-mediator limit
+ * F_DM = 1, m_med_eV == 0 the light limit (alpha m_e / q)^2, otherwise the
+ * full form factor of Eq. (F_DM).  The ionisation model is the step
+ * Q(w) = 1 + floor((w - w_gap)/w_pp) for w >= w_gap. */
+typedef struct {
+    double m_chi_eV;          /* dark-matter mass                         */
+    double sigma_e_cm2;       /* reference cross section sigma_e          */
+    double rho_chi_GeV_cm3;   /* local dark-matter density                */
+    double v0_kms;            /* Maxwellian velocity dispersion parameter */
+    double vesc_kms;          /* galactic escape speed                    */
+    double vE_kms;            /* Earth speed in the galactic frame        */
+    double rho_T_g_cm3;       /* target mass density                      */
+    double m_med_eV;          /* mediator mass (see above)                */
+    double w_gap_eV;          /* ionisation threshold                     */
+    double w_pp_eV;           /* energy per extra electron-hole pair      */
+} qcx_halo_params;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` using `cuda_stream` (a
+ * cudaStream_t; NULL = a new non-blocking stream owned by the context).
+ * Errors: QCX_ERR_ARG (out == NULL), QCX_ERR_CUDA (device unusable or not
+ * sm_103), QCX_ERR_ALLOC. */
+qcx_status qcx_create(qcx_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer the context owns.  NULL is ignored. */
+void qcx_destroy(qcx_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none).  Valid
+ * until the next call on the context. */
+const char* qcx_last_error(const qcx_ctx* ctx);
+
+/* Wait for all work queued on the context's stream. */
+qcx_status qcx_sync(qcx_ctx* ctx);
+
+/* --------------------------------------------------------------- system */
+
+/* Crystal and Gaussian basis (Sec. III: localized Gaussian orbitals).
+ * lattice[9]: rows a_1, a_2, a_3 (bohr).  The lattice must be a sublattice
+ * of h Z^3 for some spacing h with all three Cartesian axes equal (simple,
+ * face-centred and body-centred cubic in the cubic frame); otherwise
+ * QCX_ERR_UNSUPPORTED.  atom_xyz[natom][3] (bohr).  Shells: shell_atom[s]
+ * in [0, natom), shell_l[s] in {0, 1}, shell_exp[s] > 0 (bohr^-2); an l = 1
+ * shell contributes p_x, p_y, p_z in that order, normalised primitives.
+ * Replaces any previous basis and drops all states.
+ * Errors: QCX_ERR_ARG, QCX_ERR_UNSUPPORTED, QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_set_basis(qcx_ctx* ctx, const double* lattice, int natom, const double* atom_xyz,
+                         int nshell, const int* shell_atom, const int* shell_l, const double* shell_exp);
+
+/* Number of basis functions n_b of the current basis (0 if none). */
+int qcx_nbasis(const qcx_ctx* ctx);
+
+/* Bloch-sum overlap S_mu,nu(k) = <phi_mu k|phi_nu k> for nk points
+ * kpts[nk][3] (bohr^-1), written to out_S[nk][nb][nb] (row mu, column nu).
+ * This is the G = 0, q = 0 matrix element of Eq. (RPA), used to
+ * orthonormalise coefficients.  Errors: QCX_ERR_STATE (no basis), QCX_ERR_ARG. */
+qcx_status qcx_overlap(qcx_ctx* ctx, int nk, const double* kpts, qcx_c64* out_S);
+
+/* Bloch coefficients and band energies (Eq. (RPA) states; T = 0, valence
+ * f = 2, conduction f = 0).
+ *   kpts[nk][3]            initial-state k grid (bohr^-1)
+ *   C_k[nk][nb][nv]        valence coefficients at k, column v = band
+ *   E_k[nk][nv]            valence energies (Hartree)
+ *   qpts[nq][3]            momentum shifts q (the final-state grid is k + q)
+ *   C_kq[nq][nk][nb][nc]   conduction coefficients at k + q
+ *   E_kq[nq][nk][nc]       conduction energies (Hartree)
+ * Coefficients are used as given (orthonormality is the caller's; see
+ * qcx_overlap).  Replaces earlier states.  Errors: QCX_ERR_STATE (no
+ * basis), QCX_ERR_ARG, QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, const qcx_c64* C_k,
+                          const double* E_k, int nq, const double* qpts, int nc, const qcx_c64* C_kq,
+                          const double* E_kq);
+
+/* ------------------------------------------------------------ the path */
+
+/* Pair densities for q number iq and the G set G_int[ng][3]
+ * (Eq. (RPA) matrix elements; closed-form Gaussian-product integrals with
+ * the lattice sum done as separable one-dimensional sums).  The result is
+ * kept in the context (FP64 for QCX_FP64; FP32 values stored as BF16
+ * hi/lo pairs for QCX_MIXED) and, if out_rho != NULL, also written to
+ * out_rho[nt][ng] (complex double).  Starts a new q: the context's chi0,
+ * eps and loss tables for other q are untouched; those for iq are reset.
+ * Errors: QCX_ERR_STATE (no states), QCX_ERR_ARG (iq, ng < 1, ng > 4096),
+ * QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_precision prec,
+                            qcx_c64* out_rho);
+
+/* chi0_GG'(q,w) for nw frequencies w[nw] (Hartree) and broadening eta > 0
+ * (Eq. (RPA)), followed in the same kernel by the Dyson step
+ * eps = 1 - v^1/2 chi0 v^1/2, kept in the context.  Needs
+ * qcx_pair_density(iq) in the same precision.  out_chi0[nw][ng][ng]
+ * (row G, column G') is optional.  Errors: QCX_ERR_STATE, QCX_ERR_ARG
+ * (nw < 1, eta <= 0, non-finite w), QCX_ERR_ALLOC, QCX_ERR_CUDA,
+ * QCX_ERR_TIMEOUT (a pipeline wait gave up; results are invalid). */
+qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, qcx_precision prec,
+                    qcx_c64* out_chi0);
+
+/* Inverse of every eps(w) of the last qcx_chi0(iq) call: Gauss-Jordan with
+ * partial pivoting (FP64, or FP32 followed by one FP64 residual correction
+ * of the diagonal for QCX_MIXED).  Writes, if not NULL,
+ *   out_diag_inv[nw][ng]   [eps^-1]_GG                     (Eq. (eps_LFE))
+ *   out_eps_diag[nw][ng]   eps_GG                          (Eq. (eps_noLFE))
+ *   out_resid[nw]          max_G |correction| / |[eps^-1]_GG| of the FP64
+ *                          step (QCX_MIXED), 0 for QCX_FP64.
+ * and keeps the loss tables of iq in the context.
+ * Errors: QCX_ERR_STATE, QCX_ERR_SINGULAR (zero pivot in some block; the
+ * other blocks are valid), QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out_diag_inv,
+                          qcx_c64* out_eps_diag, double* out_resid);
+
+/* Loss functions of q number iq (Eq. (dynamic_structure_factor)):
+ *   out_L_lfe[nw][ng]   = -Im [eps^-1]_GG   (with local fields)
+ *   out_L_nolfe[nw][ng] = -Im (1/eps_GG)    (without)
+ * Needs qcx_invert_eps(iq).  Errors: QCX_ERR_STATE, QCX_ERR_CUDA. */
+qcx_status qcx_loss_function(qcx_ctx* ctx, int iq, double* out_L_lfe, double* out_L_nolfe);
+
+/* Average the stored loss tables of the listed q over |q+G| bins
+ * (momentum q + G carries [eps^-1]_GG by Eq. (eps_LFE)).  which = 0: with
+ * local fields, 1: without.  edges[nbin+1] ascending (bohr^-1).  All listed
+ * q must share nw and the frequency grid.  out_L[nbin][nw] is the bin mean
+ * (0 for empty bins), out_count[nbin] the number of (q, G) per bin.
+ * Errors: QCX_ERR_STATE (a q without loss table), QCX_ERR_ARG. */
+qcx_status qcx_bin_loss(qcx_ctx* ctx, int nsel, const int* iq_list, int which, int nbin,
+                        const double* edges, double* out_L, double* out_count);
+
+/* Nonrelativistic halo rate dR/dw = (rho_chi/m_chi)(1/rho_T) sigma_e/(8 pi^2
+ * alpha mu^2) int dq q^3 |F_DM|^2 L(w,q) eta(v_min) (end of Appendix A with
+ * Eqs. (general_rate), (v_min)), composite trapezoid over qbin[nqbin]
+ * (ascending, bohr^-1) with L[nqbin][nw]; w[nw] uniform (Hartree).
+ * out_dRdw[nw] in events/(kg yr eV); out_dRQ[nQ] = sum_w dR/dw dw over
+ * Q(w) = 1..nQ (Eq. (excitation_rate)) in events/(kg yr).  Accumulation in
+ * FP64.  Errors: QCX_ERR_ARG. */
+qcx_status qcx_rate(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const double* w,
+                    const double* L, const qcx_halo_params* params, double* out_dRdw, int nQ,
+                    double* out_dRQ);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCX_H */

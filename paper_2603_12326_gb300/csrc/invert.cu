@@ -1,0 +1,286 @@
+// Inverse of the dielectric matrices and the loss functions.
+//
+// eps(w, q+G) = 1/[eps^-1]_GG (Eq. (eps_LFE)); eps^noLFE = eps_GG
+// (Eq. (eps_noLFE)); L = Im[-1/eps] (Eq. (dynamic_structure_factor)).
+//
+// One CTA per (q, w) block runs Gauss-Jordan elimination with partial
+// (row) pivoting in place on a work copy of the matrix, then undoes the
+// column permutation.  The FP64 path does this in double.  The mixed path
+// does it in FP32 and then applies one FP64 correction of the diagonal:
+// with R = I - A X (computed in FP64 from the FP32 A and X, whose products
+// are exact in FP64), [A^-1]_jj = X_jj + (X R)_jj + O(|R|^2).
+#include "qcx_internal.h"
+#include "cplx.cuh"
+
+namespace {
+
+constexpr int INV_THREADS = 512;
+
+template <typename T> struct InvArgs {
+    int ng, nw;
+    const double2* eps64;      // FP64 input [nw][ng][ng]
+    const float* eps_re;       // FP32 planar input [nw][ng][ng]
+    const float* eps_im;
+    cplx<T>* X;                // work [nw][ng][ng]
+    double2* diag_inv;         // [nw][ng]
+    double2* eps_diag;         // [nw][ng]
+    double* L;                 // [2][nw][ng] (LFE, noLFE)
+    int* flags;                // [nw]
+};
+
+template <typename T> __device__ __forceinline__ T cabs2(cplx<T> z) { return z.x * z.x + z.y * z.y; }
+
+template <typename T>
+__global__ void __launch_bounds__(INV_THREADS) k_gauss_jordan(InvArgs<T> a, int write_lfe) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.ng;
+    C* rowk = reinterpret_cast<C*>(smem_raw);          // [n]
+    C* colk = rowk + n;                                 // [n]
+    int* piv = reinterpret_cast<int*>(colk + n);        // [n]
+    int* idx = piv + n;                                 // [n]
+    __shared__ T red_v[INV_THREADS / 32];
+    __shared__ int red_i[INV_THREADS / 32];
+    __shared__ int s_p;
+    __shared__ int s_bad;
+
+    const int b = blockIdx.x;
+    C* X = a.X + (size_t)b * n * n;
+    // load the matrix; record eps_GG and the loss without local fields
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        C v;
+        if (a.eps64) {
+            const double2 z = a.eps64[(size_t)b * n * n + e];
+            v = mk<T>((T)z.x, (T)z.y);
+        } else {
+            v = mk<T>((T)a.eps_re[(size_t)b * n * n + e], (T)a.eps_im[(size_t)b * n * n + e]);
+        }
+        X[e] = v;
+        const int i = e / n;
+        if (e == i * n + i) {
+            const double re = (double)v.x, im = (double)v.y;
+            a.eps_diag[(size_t)b * n + i] = make_double2(re, im);
+            a.L[((size_t)a.nw + b) * n + i] = im / (re * re + im * im);
+        }
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+
+    for (int k = 0; k < n; ++k) {
+        // pivot: largest |X_ik| over i >= k (smallest index on ties)
+        T best = -1;
+        int bi = n;
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            const T v = cabs2<T>(X[(size_t)i * n + k]);
+            if (v > best) {
+                best = v;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            red_v[wid] = best;
+            red_i[wid] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T bv = red_v[0];
+            int bix = red_i[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bix)) {
+                    bv = red_v[w];
+                    bix = red_i[w];
+                }
+            if (!(bv > 0) || bix >= n) {
+                s_bad = 1;
+                bix = k;
+            }
+            s_p = bix;
+            piv[k] = bix;
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int p = s_p;
+        // swap rows k and p, then load the (scaled) pivot row and column k
+        if (p != k) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const C t = X[(size_t)k * n + j];
+                X[(size_t)k * n + j] = X[(size_t)p * n + j];
+                X[(size_t)p * n + j] = t;
+            }
+            __syncthreads();
+        }
+        const C pv = X[(size_t)k * n + k];
+        const T d = (T)1 / cabs2<T>(pv);
+        const C inv = mk<T>(pv.x * d, -pv.y * d);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const C v = (j == k) ? mk<T>(1, 0) : X[(size_t)k * n + j];
+            rowk[j] = cmul(v, inv);
+            colk[j] = (j == k) ? mk<T>(0, 0) : X[(size_t)j * n + k];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) X[(size_t)k * n + j] = rowk[j];
+        // eliminate column k from every other row; X_ik itself becomes -colk_i * inv
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e / n, j = e - i * n;
+            if (i == k) continue;
+            const C f = colk[i];
+            C x = (j == k) ? mk<T>(0, 0) : X[e];
+            x.x -= f.x * rowk[j].x - f.y * rowk[j].y;
+            x.y -= f.x * rowk[j].y + f.y * rowk[j].x;
+            X[e] = x;
+        }
+        __syncthreads();
+    }
+    if (s_bad) {
+        if (threadIdx.x == 0) a.flags[b] = 1;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            a.diag_inv[(size_t)b * n + j] = make_double2(0.0, 0.0);
+            if (write_lfe) a.L[(size_t)b * n + j] = 0.0;
+        }
+        return;
+    }
+    // undo the column permutation: the inverse's column c is X's column idx[c]
+    if (threadIdx.x == 0) {
+        a.flags[b] = 0;
+        for (int c = 0; c < n; ++c) idx[c] = c;
+        for (int k = n - 1; k >= 0; --k) {
+            const int t = idx[k];
+            idx[k] = idx[piv[k]];
+            idx[piv[k]] = t;
+        }
+    }
+    __syncthreads();
+    // write the permuted inverse back in place, row by row through shared memory
+    for (int i = 0; i < n; ++i) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) rowk[j] = X[(size_t)i * n + idx[j]];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) X[(size_t)i * n + j] = rowk[j];
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const C z = X[(size_t)j * n + j];
+        a.diag_inv[(size_t)b * n + j] = make_double2((double)z.x, (double)z.y);
+        if (write_lfe) a.L[(size_t)b * n + j] = -(double)z.y;
+    }
+}
+
+// FP64 correction of the diagonal of X = A^-1 (A planar FP32, X FP32):
+//   d_j = X_jj + sum_k X_jk (delta_kj - sum_l A_kl X_lj).
+// One CTA per block; 32-column panels; each thread owns (row k, column j)
+// pairs of the panel and accumulates in FP64.
+constexpr int RF_COLS = 32;
+__global__ void __launch_bounds__(256) k_refine_diag(int n, int nw, const float* eps_re, const float* eps_im,
+                                                     const float2* Xall, const int* flags, double2* diag_inv,
+                                                     double* L, double* resid) {
+    __shared__ double2 s_d[RF_COLS];
+    __shared__ double s_rel[RF_COLS];
+    const int b = blockIdx.x;
+    if (flags[b]) {
+        if (threadIdx.x == 0) resid[b] = 0.0;
+        return;
+    }
+    const float* Ar = eps_re + (size_t)b * n * n;
+    const float* Ai = eps_im + (size_t)b * n * n;
+    const float2* X = Xall + (size_t)b * n * n;
+    double worst = 0.0;
+    for (int j0 = 0; j0 < n; j0 += RF_COLS) {
+        if (threadIdx.x < RF_COLS) s_d[threadIdx.x] = make_double2(0.0, 0.0);
+        __syncthreads();
+        const int jl = threadIdx.x & (RF_COLS - 1);
+        const int j = j0 + jl;
+        double2 part = make_double2(0.0, 0.0);
+        if (j < n) {
+            for (int k = threadIdx.x / RF_COLS; k < n; k += blockDim.x / RF_COLS) {
+                // y = sum_l A_kl X_lj  (FP64)
+                double yr = 0.0, yi = 0.0;
+                for (int l = 0; l < n; ++l) {
+                    const double ar = Ar[(size_t)k * n + l], ai = Ai[(size_t)k * n + l];
+                    const float2 x = X[(size_t)l * n + j];
+                    yr = fma(ar, (double)x.x, yr);
+                    yr = fma(-ai, (double)x.y, yr);
+                    yi = fma(ar, (double)x.y, yi);
+                    yi = fma(ai, (double)x.x, yi);
+                }
+                const double rr = (k == j ? 1.0 : 0.0) - yr, ri = -yi;
+                const float2 xjk = X[(size_t)j * n + k];
+                part.x += (double)xjk.x * rr - (double)xjk.y * ri;
+                part.y += (double)xjk.x * ri + (double)xjk.y * rr;
+            }
+        }
+        atomicAdd(&s_d[jl].x, part.x);
+        atomicAdd(&s_d[jl].y, part.y);
+        __syncthreads();
+        if (threadIdx.x < RF_COLS && j0 + threadIdx.x < n) {
+            const int jj = j0 + threadIdx.x;
+            const float2 x = X[(size_t)jj * n + jj];
+            const double dr = (double)x.x + s_d[threadIdx.x].x, di = (double)x.y + s_d[threadIdx.x].y;
+            diag_inv[(size_t)b * n + jj] = make_double2(dr, di);
+            L[(size_t)b * n + jj] = -di;
+            const double mag = sqrt(dr * dr + di * di);
+            s_rel[threadIdx.x] = mag > 0 ? sqrt(s_d[threadIdx.x].x * s_d[threadIdx.x].x +
+                                                s_d[threadIdx.x].y * s_d[threadIdx.x].y) / mag
+                                         : 0.0;
+        } else if (threadIdx.x < RF_COLS) {
+            s_rel[threadIdx.x] = 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int c = 0; c < RF_COLS; ++c) worst = fmax(worst, s_rel[c]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) resid[b] = worst;
+}
+
+}  // namespace
+
+cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double* d_loss_out) {
+    const int n = s.ng;
+    if (prec == QCX_FP64) {
+        InvArgs<double> a{};
+        a.ng = n;
+        a.nw = s.nw;
+        a.eps64 = s.eps.as<double2>();
+        a.X = s.work.as<double2>();
+        a.diag_inv = s.diag_inv.as<double2>();
+        a.eps_diag = s.eps_diag.as<double2>();
+        a.L = d_loss_out;
+        a.flags = s.flags.as<int>();
+        const size_t smem = (size_t)n * 2 * sizeof(double2) + (size_t)n * 2 * sizeof(int);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_gauss_jordan<double>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gauss_jordan<double><<<s.nw, INV_THREADS, smem, ctx->stream>>>(a, 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return cudaMemsetAsync(s.resid.p, 0, sizeof(double) * s.nw, ctx->stream);
+    }
+    InvArgs<float> a{};
+    a.ng = n;
+    a.nw = s.nw;
+    a.eps_re = s.eps.as<float>();
+    a.eps_im = s.eps.as<float>() + (size_t)s.nw * n * n;
+    a.X = s.work.as<float2>();
+    a.diag_inv = s.diag_inv.as<double2>();
+    a.eps_diag = s.eps_diag.as<double2>();
+    a.L = d_loss_out;
+    a.flags = s.flags.as<int>();
+    const size_t smem = (size_t)n * 2 * sizeof(float2) + (size_t)n * 2 * sizeof(int);
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_gauss_jordan<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gauss_jordan<float><<<s.nw, INV_THREADS, smem, ctx->stream>>>(a, 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_refine_diag<<<s.nw, 256, 0, ctx->stream>>>(n, s.nw, a.eps_re, a.eps_im, a.X, a.flags, a.diag_inv,
+                                                  d_loss_out, s.resid.as<double>());
+    return cudaGetLastError();
+}

@@ -1,0 +1,507 @@
+// Pair densities rho_vck(q+G) = <c,k+q| e^{i(q+G).r} |v,k>  (Eq. (RPA) matrix
+// elements; Bloch form of Appendix C) for Bloch sums of normalised Cartesian
+// s/p Gaussians.
+//
+// Per (k, G) and shell pair (a on centre A, b on centre B):
+//   B_ab(k; kappa) = sum_L e^{ik.L} int chi_a(r-A) e^{i kappa.r} chi_b(r-B-L) dr.
+// With the Gaussian product theorem every term is a product over the three
+// Cartesian axes.  The lattice is a sublattice of index m of h Z^3, so the
+// sum over L is (1/m) sum_chi sum_{n in Z^3} chi(n) F(h n), and the Z^3 sum of
+// a product is the product of three one-dimensional sums.  Per axis
+//   sum_n e^{i theta n} w_n d_n^j ,  d_n = A_x - B_x - h n,  w_n = e^{-mu d_n^2},
+//   theta = (k_x + (beta/p) kappa_x) h + 2 pi chi_x,   j = 0, 1, 2,
+// gives the one-dimensional factors E(l_a, l_b) of the closed form
+// (E(0,0) = 1, E(1,0) = PA + i kappa/2p, E(0,1) = PB + i kappa/2p,
+//  E(1,1) = PA PB + (PA + PB) i kappa/2p + 1/2p - kappa^2/4p^2 with
+//  PA = -(beta/p) d, PB = (alpha/p) d).
+// The contraction rho = C_kq^H B C_k runs in shared memory per (k, G).
+#include "qcx_internal.h"
+#include "cplx.cuh"
+
+#include <cmath>
+
+namespace {
+
+constexpr int PD_THREADS = 256;
+constexpr double LATTICE_CUT = 46.0;   // Gaussian prefactors below e^-46 ~ 1e-20 are dropped
+
+template <typename T> struct PDArgs {
+    int nb, nv, nc, nk, ng, nt, ldB, nshell;
+    int row_s0[65];          // shell row blocks: shells [row_s0[i], row_s0[i+1])
+    int nblk;
+    int max_rows;            // rows of the largest block (Bs holds max_rows * ldB entries)
+    int g_per_cta;
+    T h;
+    T charang[4][3];
+    const int* shell_l;
+    const int* shell_mu0;
+    const int* dir_off;      // [npair][3]
+    const int* dir_cnt;
+    const int* dir_nlo;
+    const T* par;            // [npair][8]
+    const cplx<T>* tab;      // terms {w_n, d_n}
+    const T* kpts;           // [nk][3]
+    const T* kappa;          // [ng][3]
+    const cplx<T>* Ck;       // [nk][nb][nv]
+    const cplx<T>* Ckq;      // [nk][nb][nc]
+    double2* R64;            // FP64 output [ng][nt]
+    __nv_bfloat162* Rhi;     // MIXED output planes [ngp][kp/2] (bf16 pairs re, im)
+    __nv_bfloat162* Rlo;
+    long long kp2;           // row length of the bf16 planes in bf16x2 units
+    cplx<T>* Sout;           // overlap mode: [nk][nb][nb]
+};
+
+// One shell pair's block of B into shared memory (row offset row0).
+template <typename T, int NCH>
+__device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T kk[3], const T kap[3], T k2,
+                                           cplx<T>* Bs, int row0) {
+    using C = cplx<T>;
+    const int sa = ip / a.nshell, sb = ip % a.nshell;
+    const T* par = a.par + (size_t)ip * 8;
+    const T p = par[0], ap = par[1], bp = par[2], pref = par[3];
+    const int la = a.shell_l[sa], lb = a.shell_l[sb];
+    const T inv2p = T(0.5) / p;
+    T s, c;
+    sincos_t(kap[0] * par[4] + kap[1] * par[5] + kap[2] * par[6], &s, &c);
+    const T amp = pref * exp_t(-k2 * T(0.25) / p) / T(NCH);
+    const C common = mk<T>(amp * c, amp * s);
+
+    C E[3][NCH][4];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const int di = ip * 3 + x;
+        const int off = a.dir_off[di], cnt = a.dir_cnt[di], nlo = a.dir_nlo[di];
+        const T theta = (kk[x] + bp * kap[x]) * a.h;
+        const T tk = kap[x] * inv2p;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            const T phi = theta + a.charang[ch][x];
+            T zs, zc, ss, cc;
+            sincos_t(phi, &zs, &zc);
+            sincos_t(phi * T(nlo), &ss, &cc);
+            C zn = mk<T>(cc, ss);
+            const C z = mk<T>(zc, zs);
+            C M0 = mk<T>(0, 0), M1 = mk<T>(0, 0), M2 = mk<T>(0, 0);
+            for (int j = 0; j < cnt; ++j) {
+                const C wd = a.tab[off + j];
+                const C t0 = cscale(zn, wd.x);
+                M0 = cadd(M0, t0);
+                const C t1 = cscale(t0, wd.y);
+                M1 = cadd(M1, t1);
+                M2 = cadd(M2, cscale(t1, wd.y));
+                zn = cmul(zn, z);
+            }
+            const C itkM0 = mk<T>(-tk * M0.y, tk * M0.x);
+            const C itkM1 = mk<T>(-tk * M1.y, tk * M1.x);
+            C e0 = M0;
+            C e1 = cadd(cscale(M1, -bp), itkM0);                       // E(1,0)
+            C e2 = cadd(cscale(M1, ap), itkM0);                        // E(0,1)
+            C e3 = cadd(cadd(cscale(M2, -ap * bp), cscale(itkM1, ap - bp)),
+                        cscale(M0, inv2p - tk * tk));                  // E(1,1)
+            // an s function on one side makes the l = 1 slots equal to the l = 0 ones,
+            // so the component loop below can index with compile-time selectors
+            if (!la) { e1 = e0; e3 = e2; }
+            if (!lb) { e2 = e0; e3 = e1; }
+            E[x][ch][0] = e0;
+            E[x][ch][1] = e1;
+            E[x][ch][2] = e2;
+            E[x][ch][3] = e3;
+        }
+    }
+    const int na = la ? 3 : 1, nbn = lb ? 3 : 1;
+    const int mu0 = a.shell_mu0[sa] - row0, nu0 = a.shell_mu0[sb];
+#pragma unroll
+    for (int ia = 0; ia < 3; ++ia) {
+#pragma unroll
+        for (int ib = 0; ib < 3; ++ib) {
+            if (ia < na && ib < nbn) {
+                C val = mk<T>(0, 0);
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    C prod = E[0][ch][(ia == 0) + 2 * (ib == 0)];
+                    prod = cmul(prod, E[1][ch][(ia == 1) + 2 * (ib == 1)]);
+                    prod = cmul(prod, E[2][ch][(ia == 2) + 2 * (ib == 2)]);
+                    val = cadd(val, prod);
+                }
+                Bs[(mu0 + ia) * a.ldB + nu0 + ib] = cmul(common, val);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+template <typename T, int NCH>
+__global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* Bs = reinterpret_cast<C*>(smem_raw);        // [max_rows][ldB]
+    C* Cks = Bs + (size_t)a.max_rows * a.ldB;      // [nb][nv]
+    C* Ys = Cks + (size_t)a.nb * a.nv;             // [nb][nv]
+
+    const int k = blockIdx.x;
+    for (int i = threadIdx.x; i < a.nb * a.nv; i += blockDim.x) Cks[i] = a.Ck[(size_t)k * a.nb * a.nv + i];
+    const T kk[3] = {a.kpts[3 * k], a.kpts[3 * k + 1], a.kpts[3 * k + 2]};
+    const C* Ckq = a.Ckq + (size_t)k * a.nb * a.nc;
+    const int g0 = blockIdx.y * a.g_per_cta;
+    const int g1 = min(a.ng, g0 + a.g_per_cta);
+
+    for (int g = g0; g < g1; ++g) {
+        const T kap[3] = {a.kappa[3 * g], a.kappa[3 * g + 1], a.kappa[3 * g + 2]};
+        const T k2 = kap[0] * kap[0] + kap[1] * kap[1] + kap[2] * kap[2];
+        for (int blk = 0; blk < a.nblk; ++blk) {
+            const int s0 = a.row_s0[blk], s1 = a.row_s0[blk + 1];
+            const int row0 = a.shell_mu0[s0];
+            const int row1 = s1 < a.nshell ? a.shell_mu0[s1] : a.nb;
+            __syncthreads();  // Bs free, Cks staged
+            const int p0 = s0 * a.nshell, p1 = s1 * a.nshell;
+            for (int ip = p0 + threadIdx.x; ip < p1; ip += blockDim.x) pair_block<T, NCH>(a, ip, kk, kap, k2, Bs, row0);
+            __syncthreads();
+            const int rows = row1 - row0;
+            for (int i = threadIdx.x; i < rows * a.nv; i += blockDim.x) {
+                const int r = i / a.nv, v = i - r * a.nv;
+                C acc = mk<T>(0, 0);
+                const C* brow = Bs + (size_t)r * a.ldB;
+                for (int nu = 0; nu < a.nb; ++nu) cfma(acc, brow[nu], Cks[nu * a.nv + v]);
+                Ys[(row0 + r) * a.nv + v] = acc;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < a.nv * a.nc; i += blockDim.x) {
+            const int v = i / a.nc, c = i - v * a.nc;
+            C acc = mk<T>(0, 0);
+            for (int mu = 0; mu < a.nb; ++mu) cfmac(acc, Ckq[mu * a.nc + c], Ys[mu * a.nv + v]);
+            const long long t = ((long long)k * a.nv + v) * a.nc + c;
+            if (a.R64) {
+                a.R64[(long long)g * a.nt + t] = make_double2((double)acc.x, (double)acc.y);
+            } else {
+                __nv_bfloat16 hr, lr, hi_, li;
+                split_bf16((float)acc.x, hr, lr);
+                split_bf16((float)acc.y, hi_, li);
+                a.Rhi[(long long)g * a.kp2 + t] = __halves2bfloat162(hr, hi_);
+                a.Rlo[(long long)g * a.kp2 + t] = __halves2bfloat162(lr, li);
+            }
+        }
+    }
+}
+
+// S(k) = B(k; 0): one CTA per k, full matrix written to Sout.
+template <typename T, int NCH>
+__global__ void __launch_bounds__(PD_THREADS) k_overlap(PDArgs<T> a) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* Bs = reinterpret_cast<C*>(smem_raw);
+    const int k = blockIdx.x;
+    const T kk[3] = {a.kpts[3 * k], a.kpts[3 * k + 1], a.kpts[3 * k + 2]};
+    const T kap[3] = {0, 0, 0};
+    for (int blk = 0; blk < a.nblk; ++blk) {
+        const int s0 = a.row_s0[blk], s1 = a.row_s0[blk + 1];
+        const int row0 = a.shell_mu0[s0];
+        const int row1 = s1 < a.nshell ? a.shell_mu0[s1] : a.nb;
+        __syncthreads();
+        for (int ip = s0 * a.nshell + threadIdx.x; ip < s1 * a.nshell; ip += blockDim.x)
+            pair_block<T, NCH>(a, ip, kk, kap, T(0), Bs, row0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < (row1 - row0) * a.nb; i += blockDim.x) {
+            const int r = i / a.nb, nu = i - r * a.nb;
+            a.Sout[((size_t)k * a.nb + row0 + r) * a.nb + nu] = Bs[(size_t)r * a.ldB + nu];
+        }
+    }
+}
+
+__global__ void k_qsetup(const int* G, int ng, double q0, double q1, double q2, double b00, double b01,
+                         double b02, double b10, double b11, double b12, double b20, double b21, double b22,
+                         double* kappa, float* kappa32, double* vs, float* vs32) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const double n0 = G[3 * g], n1 = G[3 * g + 1], n2 = G[3 * g + 2];
+        const double x = q0 + n0 * b00 + n1 * b10 + n2 * b20;
+        const double y = q1 + n0 * b01 + n1 * b11 + n2 * b21;
+        const double z = q2 + n0 * b02 + n1 * b12 + n2 * b22;
+        kappa[3 * g] = x;
+        kappa[3 * g + 1] = y;
+        kappa[3 * g + 2] = z;
+        kappa32[3 * g] = (float)x;
+        kappa32[3 * g + 1] = (float)y;
+        kappa32[3 * g + 2] = (float)z;
+        const double v = QCX_SQRT_4PI / sqrt(x * x + y * y + z * z);
+        vs[g] = v;
+        vs32[g] = (float)v;
+    }
+}
+
+template <typename T> void fill_common(qcx_ctx* ctx, PDArgs<T>& a) {
+    a.nb = ctx->nb;
+    a.nshell = ctx->nshell;
+    a.h = (T)ctx->h;
+    for (int c = 0; c < 4; ++c)
+        for (int x = 0; x < 3; ++x) a.charang[c][x] = (T)(2.0 * M_PI * ctx->chars[c][x]);
+    a.shell_l = ctx->d_shell_l.as<int>();
+    a.shell_mu0 = ctx->d_shell_mu0.as<int>();
+    const PairTables& pt = ctx->pairs;
+    a.dir_off = pt.dir_off.as<int>();
+    a.dir_cnt = pt.dir_cnt.as<int>();
+    a.dir_nlo = pt.dir_nlo.as<int>();
+}
+
+// Row blocks of shells such that the B rows plus Ck and Y fit in `budget` bytes.
+template <typename T> int plan_blocks(qcx_ctx* ctx, PDArgs<T>& a, int nv, size_t* smem) {
+    const size_t cs = sizeof(cplx<T>);
+    const size_t budget = 200 * 1024;
+    const size_t fixed = 2 * (size_t)ctx->nb * nv * cs;
+    const int ldB = ctx->nb + 1;
+    if (fixed + 3 * ldB * cs > budget) return -1;
+    const size_t max_rows = (budget - fixed) / (ldB * cs);
+    a.ldB = ldB;
+    int nblk = 0, s = 0, rows_max = 0;
+    a.row_s0[0] = 0;
+    while (s < ctx->nshell) {
+        int rows = 0, e = s;
+        while (e < ctx->nshell) {
+            const int r = ctx->shell_l[e] ? 3 : 1;
+            if (rows + r > (int)max_rows) break;
+            rows += r;
+            ++e;
+        }
+        if (e == s) return -1;
+        if (nblk >= 64) return -1;
+        a.row_s0[++nblk] = e;
+        rows_max = rows > rows_max ? rows : rows_max;
+        s = e;
+    }
+    a.nblk = nblk;
+    a.max_rows = rows_max;
+    *smem = fixed + (size_t)rows_max * ldB * cs;
+    return 0;
+}
+
+template <typename T> cudaError_t set_smem(const void* fn, size_t smem) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T, int NCH> cudaError_t launch_pd(qcx_ctx* ctx, PDArgs<T>& a, size_t smem, dim3 grid) {
+    cudaError_t e = set_smem<T>((const void*)k_pair_density<T, NCH>, smem);
+    if (e != cudaSuccess) return e;
+    k_pair_density<T, NCH><<<grid, PD_THREADS, smem, ctx->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int NCH> cudaError_t launch_ov(qcx_ctx* ctx, PDArgs<T>& a, size_t smem, int nk) {
+    cudaError_t e = set_smem<T>((const void*)k_overlap<T, NCH>, smem);
+    if (e != cudaSuccess) return e;
+    k_overlap<T, NCH><<<nk, PD_THREADS, smem, ctx->stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------- host
+
+// Recognise lattice subset h Z^3 and its characters; build the per-pair
+// one-dimensional tables.  Returns QCX_OK or an error with ctx->err set.
+qcx_status qcx_build_pair_tables(qcx_ctx* ctx) {
+    const double* L = ctx->lattice;
+    double hmin = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        const double v = fabs(L[i]);
+        if (v > 1e-9 && (hmin == 0.0 || v < hmin)) hmin = v;
+    }
+    if (hmin == 0.0) return ctx->fail(QCX_ERR_ARG, "lattice is zero");
+    double h = 0.0;
+    int M[9];
+    for (int div = 1; div <= 6 && h == 0.0; ++div) {
+        const double hc = hmin / div;
+        bool ok = true;
+        for (int i = 0; i < 9 && ok; ++i) {
+            const double r = L[i] / hc;
+            const double n = std::round(r);
+            if (fabs(r - n) > 1e-8 * fmax(1.0, fabs(r))) ok = false;
+            M[i] = (int)n;
+        }
+        if (ok) h = hc;
+    }
+    if (h == 0.0)
+        return ctx->fail(QCX_ERR_UNSUPPORTED,
+                         "lattice is not a sublattice of h Z^3 (needs cubic-frame SC/FCC/BCC-type lattices)");
+    const long det = (long)M[0] * (M[4] * M[8] - M[5] * M[7]) - (long)M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                     (long)M[2] * (M[3] * M[7] - M[4] * M[6]);
+    const int m = (int)labs(det);
+    if (m < 1 || m > 4) return ctx->fail(QCX_ERR_UNSUPPORTED, "lattice index in h Z^3 must be 1..4");
+    int nch = 0;
+    for (int a0 = 0; a0 < m; ++a0)
+        for (int a1 = 0; a1 < m; ++a1)
+            for (int a2 = 0; a2 < m; ++a2) {
+                bool ok = true;
+                for (int r = 0; r < 3; ++r) {
+                    const long s = (long)M[3 * r] * a0 + (long)M[3 * r + 1] * a1 + (long)M[3 * r + 2] * a2;
+                    if (s % m != 0) ok = false;
+                }
+                if (ok && nch < 4) {
+                    ctx->chars[nch][0] = (double)a0 / m;
+                    ctx->chars[nch][1] = (double)a1 / m;
+                    ctx->chars[nch][2] = (double)a2 / m;
+                    ++nch;
+                }
+            }
+    if (nch != m) return ctx->fail(QCX_ERR_UNSUPPORTED, "could not enumerate lattice characters");
+    ctx->h = h;
+    ctx->nchar = m;
+
+    const int ns = ctx->nshell;
+    const int npair = ns * ns;
+    std::vector<int> dir_off(npair * 3), dir_cnt(npair * 3), dir_nlo(npair * 3);
+    std::vector<double> par(npair * 8);
+    std::vector<double2> tab;
+    for (int sa = 0; sa < ns; ++sa) {
+        const double al = ctx->shell_exp[sa];
+        const double* A = &ctx->atom_xyz[3 * ctx->shell_atom[sa]];
+        const double na = pow(2.0 * al / M_PI, 0.75) * (ctx->shell_l[sa] ? 2.0 * sqrt(al) : 1.0);
+        for (int sb = 0; sb < ns; ++sb) {
+            const double be = ctx->shell_exp[sb];
+            const double* B = &ctx->atom_xyz[3 * ctx->shell_atom[sb]];
+            const double nbn = pow(2.0 * be / M_PI, 0.75) * (ctx->shell_l[sb] ? 2.0 * sqrt(be) : 1.0);
+            const int ip = sa * ns + sb;
+            const double p = al + be, mu = al * be / p;
+            par[ip * 8 + 0] = p;
+            par[ip * 8 + 1] = al / p;
+            par[ip * 8 + 2] = be / p;
+            par[ip * 8 + 3] = na * nbn * pow(M_PI / p, 1.5);
+            for (int x = 0; x < 3; ++x) par[ip * 8 + 4 + x] = (al * A[x] + be * B[x]) / p;
+            par[ip * 8 + 7] = 0.0;
+            const double R = sqrt(LATTICE_CUT / mu);
+            for (int x = 0; x < 3; ++x) {
+                const double D = A[x] - B[x];
+                const int nlo = (int)std::ceil((D - R) / h);
+                const int nhi = (int)std::floor((D + R) / h);
+                dir_off[ip * 3 + x] = (int)tab.size();
+                dir_nlo[ip * 3 + x] = nlo;
+                int cnt = 0;
+                for (int n = nlo; n <= nhi; ++n) {
+                    const double d = D - h * n;
+                    tab.push_back(make_double2(exp(-mu * d * d), d));
+                    ++cnt;
+                }
+                dir_cnt[ip * 3 + x] = cnt;
+            }
+        }
+    }
+    PairTables& pt = ctx->pairs;
+    pt.npair = npair;
+    std::vector<double> par32d(par.begin(), par.end());
+    std::vector<float> par32(par.size());
+    for (size_t i = 0; i < par.size(); ++i) par32[i] = (float)par[i];
+    std::vector<float2> tab32(tab.size());
+    for (size_t i = 0; i < tab.size(); ++i) tab32[i] = make_float2((float)tab[i].x, (float)tab[i].y);
+    cudaError_t e;
+#define UP(buf, vec, T)                                                                          \
+    if ((e = buf.ensure(vec.size() * sizeof(T))) != cudaSuccess ||                                \
+        (e = cudaMemcpy(buf.p, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice)) != \
+            cudaSuccess)                                                                         \
+        return ctx->fail(QCX_ERR_CUDA, std::string("pair tables: ") + cudaGetErrorString(e));
+    UP(pt.dir_off, dir_off, int)
+    UP(pt.dir_cnt, dir_cnt, int)
+    UP(pt.dir_nlo, dir_nlo, int)
+    UP(pt.par64, par, double)
+    UP(pt.par32, par32, float)
+    UP(pt.tab64, tab, double2)
+    UP(pt.tab32, tab32, float2)
+#undef UP
+    return QCX_OK;
+}
+
+cudaError_t qcx_launch_qsetup(qcx_ctx* ctx, QSlot& s, const int* d_G, int ng, const double* q) {
+    // reciprocal basis b_i (rows) = 2 pi inv(A)^T
+    const double* A = ctx->lattice;
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    double inv[9];
+    inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+    inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+    inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    double b[9];  // b[i][j] = 2 pi inv[j][i]
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) b[3 * i + j] = 2.0 * M_PI * inv[3 * j + i];
+    k_qsetup<<<(ng + 127) / 128, 128, 0, ctx->stream>>>(d_G, ng, q[0], q[1], q[2], b[0], b[1], b[2], b[3], b[4],
+                                                         b[5], b[6], b[7], b[8], s.kappa.as<double>(),
+                                                         s.kappa32.as<float>(), s.vs.as<double>(),
+                                                         s.vs32.as<float>());
+    return cudaGetLastError();
+}
+
+cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precision prec) {
+    const int nt = ctx->nk * ctx->nv * ctx->nc;
+    const int gpc = 8;
+    dim3 grid(ctx->nk, (s.ng + gpc - 1) / gpc);
+    size_t smem = 0;
+    if (prec == QCX_FP64) {
+        PDArgs<double> a{};
+        fill_common(ctx, a);
+        if (plan_blocks(ctx, a, ctx->nv, &smem)) return cudaErrorInvalidValue;
+        a.nv = ctx->nv;
+        a.nc = ctx->nc;
+        a.nk = ctx->nk;
+        a.ng = s.ng;
+        a.nt = nt;
+        a.g_per_cta = gpc;
+        a.par = ctx->pairs.par64.as<double>();
+        a.tab = ctx->pairs.tab64.as<double2>();
+        a.kpts = ctx->d_kpts.as<double>();
+        a.kappa = s.kappa.as<double>();
+        a.Ck = ctx->d_Ck64.as<double2>();
+        a.Ckq = ctx->d_Ckq64.as<double2>() + (size_t)iq * ctx->nk * ctx->nb * ctx->nc;
+        a.R64 = s.rho.as<double2>();
+        switch (ctx->nchar) {
+            case 1: return launch_pd<double, 1>(ctx, a, smem, grid);
+            case 2: return launch_pd<double, 2>(ctx, a, smem, grid);
+            default: return launch_pd<double, 4>(ctx, a, smem, grid);
+        }
+    }
+    PDArgs<float> a{};
+    fill_common(ctx, a);
+    if (plan_blocks(ctx, a, ctx->nv, &smem)) return cudaErrorInvalidValue;
+    a.nv = ctx->nv;
+    a.nc = ctx->nc;
+    a.nk = ctx->nk;
+    a.ng = s.ng;
+    a.nt = nt;
+    a.g_per_cta = gpc;
+    a.par = ctx->pairs.par32.as<float>();
+    a.tab = ctx->pairs.tab32.as<float2>();
+    a.kpts = ctx->d_kpts32.as<float>();
+    a.kappa = s.kappa32.as<float>();
+    a.Ck = ctx->d_Ck32.as<float2>();
+    a.Ckq = ctx->d_Ckq32.as<float2>() + (size_t)iq * ctx->nk * ctx->nb * ctx->nc;
+    a.R64 = nullptr;
+    a.Rhi = reinterpret_cast<__nv_bfloat162*>(s.rho.p);
+    a.Rlo = a.Rhi + (size_t)s.ngp * (s.kp / 2);
+    a.kp2 = s.kp / 2;
+    switch (ctx->nchar) {
+        case 1: return launch_pd<float, 1>(ctx, a, smem, grid);
+        case 2: return launch_pd<float, 2>(ctx, a, smem, grid);
+        default: return launch_pd<float, 4>(ctx, a, smem, grid);
+    }
+}
+
+cudaError_t qcx_launch_overlap(qcx_ctx* ctx, int nk, const double* d_kpts, double2* d_out) {
+    PDArgs<double> a{};
+    fill_common(ctx, a);
+    size_t smem = 0;
+    if (plan_blocks(ctx, a, 0, &smem)) return cudaErrorInvalidValue;
+    a.par = ctx->pairs.par64.as<double>();
+    a.tab = ctx->pairs.tab64.as<double2>();
+    a.kpts = d_kpts;
+    a.Sout = d_out;
+    switch (ctx->nchar) {
+        case 1: return launch_ov<double, 1>(ctx, a, smem, nk);
+        case 2: return launch_ov<double, 2>(ctx, a, smem, nk);
+        default: return launch_ov<double, 4>(ctx, a, smem, nk);
+    }
+}

@@ -1,0 +1,156 @@
+// Internal declarations of libqcx (context, buffers, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "qcx.h"
+
+// ----------------------------------------------------------------- helpers
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow-only; contents are not preserved
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, n ? n : 16);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Per-precision working set of one q.
+struct QSlot {
+    int iq = -1;               // q whose pair densities are stored here
+    int ng = 0;
+    int nw = 0;
+    bool have_rho = false;
+    bool have_eps = false;
+    DevBuf kappa;              // [ng][3] double, q + G (bohr^-1)
+    DevBuf kappa32;            // [ng][3] float
+    DevBuf vs;                 // [ng] double, sqrt(4 pi)/|q+G|
+    DevBuf vs32;               // [ng] float
+    DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: hi and lo bf16 planes [ngp][kp]
+    DevBuf eps;                // FP64: [nw][ng][ng] double2 ; MIXED: re, im float planes [nw][ng][ng]
+    DevBuf work;               // inverse work space
+    DevBuf w;                  // [nw] double
+    DevBuf diag_inv;           // [nw][ng] double2
+    DevBuf eps_diag;           // [nw][ng] double2
+    DevBuf resid;              // [nw] double
+    DevBuf flags;              // [nw] int (singular / error flags)
+    int ngp = 0;               // padded G rows of the bf16 planes
+    long long kp = 0;          // padded K' = 2 nt columns of the bf16 planes
+    double eta = 0.0;
+};
+
+// Loss tables kept per q after qcx_invert_eps.
+struct LossTab {
+    int ng = 0, nw = 0;
+    DevBuf L;                  // [2][nw][ng] double: LFE then noLFE
+    DevBuf qmag;               // [ng] double |q+G|
+    std::vector<double> w;     // frequency grid (host copy, to check consistency)
+};
+
+// Separable lattice-sum tables of the basis (host-built, device copies).
+struct PairTables {
+    int npair = 0;
+    int nblk = 0;              // basis row blocks
+    std::vector<int> blk_pair_start;   // [nblk+1]
+    std::vector<int> blk_row0;         // [nblk+1] first basis row of each block
+    DevBuf meta;               // int4 per pair: {sa, sb, off_dir0, packed counts}
+    DevBuf dir_off;            // int per (pair, dir): table offset ; count in dir_cnt
+    DevBuf dir_cnt;
+    DevBuf dir_nlo;            // int per (pair, dir): first n
+    DevBuf par64;              // double per pair: {p, alpha/p, beta/p, pref, P0x, P0y, P0z, pad}
+    DevBuf par32;              // float version
+    DevBuf tab64;              // double2 per term: {w_n, d_n}
+    DevBuf tab32;              // float2
+    int max_rows = 0;          // rows of the largest block
+};
+
+struct qcx_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // basis
+    int natom = 0, nshell = 0, nb = 0;
+    double lattice[9] = {0};
+    double h = 0.0;            // orthogonal spacing with lattice subset of h Z^3
+    int nchar = 0;             // index of the lattice in h Z^3
+    double chars[4][3] = {{0}};// characters (fractions of 2 pi per unit step)
+    std::vector<double> atom_xyz;
+    std::vector<int> shell_atom, shell_l, shell_mu0;
+    std::vector<double> shell_exp;
+    DevBuf d_shell_l, d_shell_mu0;
+    PairTables pairs;
+
+    // states
+    int nk = 0, nv = 0, nc = 0, nq = 0;
+    std::vector<double> qpts;  // host copy
+    DevBuf d_kpts, d_kpts32;   // [nk][3]
+    DevBuf d_Ck64, d_Ck32;     // [nk][nb][nv]
+    DevBuf d_Ek;               // [nk][nv]
+    DevBuf d_Ckq64, d_Ckq32;   // [nq][nk][nb][nc]
+    DevBuf d_Ekq;              // [nq][nk][nc]
+
+    QSlot slot[2];             // index = qcx_precision
+    std::vector<LossTab*> loss;    // [nq]
+
+    DevBuf scratch;            // host<->device staging for outputs
+    DevBuf scratch2;
+
+    ~qcx_ctx();
+    qcx_status fail(qcx_status s, const std::string& msg) {
+        err = msg;
+        return s;
+    }
+};
+
+// ------------------------------------------------------------ small utils
+bool qcx_is_device_ptr(const void* p);
+// copy `bytes` from a host-or-device source into device memory (stream-ordered)
+cudaError_t qcx_copy_in(qcx_ctx* ctx, void* dst_dev, const void* src, size_t bytes);
+// copy device memory to a host-or-device destination; host destinations synchronise
+cudaError_t qcx_copy_out(qcx_ctx* ctx, void* dst, const void* src_dev, size_t bytes);
+
+// ---------------------------------------------------------------- launchers
+// pair densities (pair_density.cu)
+cudaError_t qcx_launch_qsetup(qcx_ctx* ctx, QSlot& s, const int* d_G, int ng, const double* q);
+cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precision prec);
+cudaError_t qcx_launch_overlap(qcx_ctx* ctx, int nk, const double* d_kpts, double2* d_out);
+cudaError_t qcx_pair_density_configure();
+
+// chi0 (chi0_fp64.cu, chi0_tc.cu)
+cudaError_t qcx_launch_chi0_fp64(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out);
+cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out, int* d_status);
+
+// inverse + loss (invert.cu)
+cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double* d_loss_out);
+
+// rate (rate.cu)
+cudaError_t qcx_launch_bin(qcx_ctx* ctx, int nsel, const double* const* d_L, const double* const* d_qmag,
+                           const int* d_ng, int nw, int which, int nbin, const double* d_edges,
+                           double* d_out, double* d_cnt);
+cudaError_t qcx_launch_rate(qcx_ctx* ctx, int nqbin, const double* d_q, int nw, const double* d_w,
+                            const double* d_L, const qcx_halo_params& p, double* d_dRdw, int nQ,
+                            double* d_dRQ);
+
+// 4 pi as used by v^1/2 = sqrt(4 pi)/|k|
+#define QCX_SQRT_4PI 3.5449077018110318

@@ -1,0 +1,233 @@
+"""ctypes binding of libqcx (include/qcx.h): argument marshalling only.
+
+The raw entry points are available under their C names (``qcx_create``,
+``qcx_pair_density``, ...) once ``load()`` has run; ``Context`` wraps them
+for numpy arrays (host memory) and torch tensors (device memory, passed by
+``data_ptr()``).  Loading fails loudly when the library has not been built:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+
+QCX_FP64 = 0
+QCX_MIXED = 1
+STATUS = {0: "QCX_OK", 1: "QCX_ERR_ARG", 2: "QCX_ERR_ALLOC", 3: "QCX_ERR_CUDA", 4: "QCX_ERR_SINGULAR",
+          5: "QCX_ERR_NOT_CONVERGED", 6: "QCX_ERR_TIMEOUT", 7: "QCX_ERR_STATE", 8: "QCX_ERR_UNSUPPORTED"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+P = ct.c_void_p
+I = ct.c_int
+D = ct.c_double
+
+
+class HaloParams(ct.Structure):
+    _fields_ = [(n, ct.c_double) for n in ("m_chi_eV", "sigma_e_cm2", "rho_chi_GeV_cm3", "v0_kms", "vesc_kms",
+                                            "vE_kms", "rho_T_g_cm3", "m_med_eV", "w_gap_eV", "w_pp_eV")]
+
+
+def halo_params(m_chi_eV=1e9, sigma_e_cm2=1e-39, rho_chi_GeV_cm3=0.3, v0_kms=238.0, vesc_kms=544.0,
+                vE_kms=250.2, rho_T_g_cm3=2.329, m_med_eV=-1.0, w_gap_eV=1.1, w_pp_eV=3.75) -> HaloParams:
+    return HaloParams(m_chi_eV, sigma_e_cm2, rho_chi_GeV_cm3, v0_kms, vesc_kms, vE_kms, rho_T_g_cm3, m_med_eV,
+                      w_gap_eV, w_pp_eV)
+
+
+_SIGS = {
+    "qcx_create": (I, [ct.POINTER(P), I, P]),
+    "qcx_destroy": (None, [P]),
+    "qcx_last_error": (ct.c_char_p, [P]),
+    "qcx_sync": (I, [P]),
+    "qcx_set_basis": (I, [P, P, I, P, I, P, P, P]),
+    "qcx_nbasis": (I, [P]),
+    "qcx_overlap": (I, [P, I, P, P]),
+    "qcx_set_states": (I, [P, I, P, I, P, P, I, P, I, P, P]),
+    "qcx_pair_density": (I, [P, I, I, P, I, P]),
+    "qcx_chi0": (I, [P, I, I, P, D, I, P]),
+    "qcx_invert_eps": (I, [P, I, I, P, P, P]),
+    "qcx_loss_function": (I, [P, I, P, P]),
+    "qcx_bin_loss": (I, [P, I, P, I, I, P, P, P]),
+    "qcx_rate": (I, [P, I, P, I, P, P, ct.POINTER(HaloParams), P, I, P]),
+}
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libqcx.so")
+
+
+def load():
+    """Load libqcx.so and bind every entry point under its C name."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqcx is not built ({path} missing): run __graft_entry__.build()")
+    lib = ct.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+        globals()[name] = f
+    _lib = lib
+    return lib
+
+
+def declared_symbols(header: str | None = None) -> list[str]:
+    """Names of the functions declared in include/qcx.h."""
+    header = header or os.path.join(os.path.dirname(_HERE), "include", "qcx.h")
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qcx_[a-z0-9_]+)\s*\(", txt)))
+
+
+class QcxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Arg:
+    """Pointer to host (numpy) or device (torch) memory of the right dtype."""
+
+    def __init__(self, x, dtype):
+        self.keep = None
+        if x is None:
+            self.ptr = None
+        elif hasattr(x, "data_ptr"):
+            import torch
+            want = {np.float64: torch.float64, np.complex128: torch.complex128, np.int32: torch.int32}[dtype]
+            if x.dtype != want or not x.is_contiguous():
+                raise TypeError(f"tensor must be contiguous {want}")
+            self.ptr = P(x.data_ptr())
+            self.keep = x
+        else:
+            arr = np.ascontiguousarray(x, dtype=dtype)
+            self.keep = arr
+            self.ptr = P(arr.ctypes.data)
+
+
+def _out(shape, dtype, out):
+    if out is not None:
+        return out
+    return np.zeros(shape, dtype=dtype)
+
+
+class Context:
+    """One libqcx context on `device` (optionally on an existing CUDA stream)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        load()
+        h = P()
+        st = qcx_create(ct.byref(h), device, P(stream) if stream else None)
+        if st:
+            raise QcxError(st, "qcx_create failed")
+        self.h = h
+        self.nk = self.nv = self.nc = self.nq = 0
+        self._ng = {}
+        self._nw = {}
+
+    def close(self):
+        if self.h:
+            qcx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st:
+            raise QcxError(st, qcx_last_error(self.h).decode())
+
+    # ---------------------------------------------------------- system
+    def set_basis(self, lattice, atom_xyz, shell_atom, shell_l, shell_exp):
+        a = [_Arg(lattice, np.float64), _Arg(atom_xyz, np.float64), _Arg(shell_atom, np.int32),
+             _Arg(shell_l, np.int32), _Arg(shell_exp, np.float64)]
+        natom = len(np.asarray(atom_xyz).reshape(-1, 3)) if not hasattr(atom_xyz, "data_ptr") else atom_xyz.shape[0]
+        nshell = len(shell_atom)
+        self._check(qcx_set_basis(self.h, a[0].ptr, natom, a[1].ptr, nshell, a[2].ptr, a[3].ptr, a[4].ptr))
+        self.nb = qcx_nbasis(self.h)
+
+    def overlap(self, kpts, out=None):
+        kp = _Arg(kpts, np.float64)
+        nk = len(kpts)
+        o = _out((nk, self.nb, self.nb), np.complex128, out)
+        oa = _Arg(o, np.complex128)
+        self._check(qcx_overlap(self.h, nk, kp.ptr, oa.ptr))
+        return o
+
+    def set_states(self, kpts, C_k, E_k, qpts, C_kq, E_kq):
+        nk, nb, nv = C_k.shape
+        nq, _, _, nc = C_kq.shape
+        a = [_Arg(kpts, np.float64), _Arg(C_k, np.complex128), _Arg(E_k, np.float64), _Arg(qpts, np.float64),
+             _Arg(C_kq, np.complex128), _Arg(E_kq, np.float64)]
+        self._check(qcx_set_states(self.h, nk, a[0].ptr, nv, a[1].ptr, a[2].ptr, nq, a[3].ptr, nc, a[4].ptr,
+                                   a[5].ptr))
+        self.nk, self.nv, self.nc, self.nq = nk, nv, nc, nq
+
+    # --------------------------------------------------------- the path
+    def pair_density(self, iq, G_int, prec=QCX_FP64, want=False, out=None):
+        g = _Arg(G_int, np.int32)
+        ng = len(G_int)
+        self._ng[prec] = ng
+        o = _out((self.nk * self.nv * self.nc, ng), np.complex128, out) if (want or out is not None) else None
+        oa = _Arg(o, np.complex128)
+        self._check(qcx_pair_density(self.h, iq, ng, g.ptr, prec, oa.ptr))
+        return o
+
+    def chi0(self, iq, w, eta, prec=QCX_FP64, want=False, out=None):
+        wa = _Arg(w, np.float64)
+        nw = len(w)
+        self._nw[prec] = nw
+        ng = self._ng.get(prec, 0)
+        o = _out((nw, ng, ng), np.complex128, out) if (want or out is not None) else None
+        oa = _Arg(o, np.complex128)
+        self._check(qcx_chi0(self.h, iq, nw, wa.ptr, float(eta), prec, oa.ptr))
+        return o
+
+    def invert_eps(self, iq, prec=QCX_FP64, want=True):
+        nw, ng = self._nw[prec], self._ng[prec]
+        if want:
+            d = np.zeros((nw, ng), np.complex128)
+            e = np.zeros((nw, ng), np.complex128)
+            r = np.zeros(nw, np.float64)
+            self._check(qcx_invert_eps(self.h, iq, prec, P(d.ctypes.data), P(e.ctypes.data), P(r.ctypes.data)))
+            return d, e, r
+        self._check(qcx_invert_eps(self.h, iq, prec, None, None, None))
+        return None
+
+    def loss_function(self, iq, prec=QCX_FP64, out_lfe=None, out_nolfe=None):
+        nw, ng = self._nw[prec], self._ng[prec]
+        a = _out((nw, ng), np.float64, out_lfe)
+        b = _out((nw, ng), np.float64, out_nolfe)
+        aa, bb = _Arg(a, np.float64), _Arg(b, np.float64)
+        self._check(qcx_loss_function(self.h, iq, aa.ptr, bb.ptr))
+        return a, b
+
+    def bin_loss(self, iq_list, which, edges, nw):
+        iq = _Arg(np.asarray(iq_list, np.int32), np.int32)
+        ed = _Arg(edges, np.float64)
+        nbin = len(edges) - 1
+        out = np.zeros((nbin, nw), np.float64)
+        cnt = np.zeros(nbin, np.float64)
+        self._check(qcx_bin_loss(self.h, len(iq_list), iq.ptr, which, nbin, ed.ptr, P(out.ctypes.data),
+                                 P(cnt.ctypes.data)))
+        return out, cnt
+
+    def rate(self, qbin, w, L, params: HaloParams, nQ=0):
+        qa, wa, La = _Arg(qbin, np.float64), _Arg(w, np.float64), _Arg(L, np.float64)
+        dR = np.zeros(len(w), np.float64)
+        dQ = np.zeros(max(nQ, 1), np.float64)
+        self._check(qcx_rate(self.h, len(qbin), qa.ptr, len(w), wa.ptr, La.ptr, ct.byref(params),
+                             P(dR.ctypes.data), nQ, P(dQ.ctypes.data) if nQ else None))
+        return dR, dQ[:nQ]
+
+    def sync(self):
+        self._check(qcx_sync(self.h))
