@@ -18,9 +18,9 @@ __global__ void k_to_float(const double* in, float* out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
 }
-// rho [ng][nt] (FP64) or bf16 hi/lo planes [ngp][kp] -> [nt][ng] double2
-__global__ void k_rho_export(int ng, long long nt, const double2* R64, const __nv_bfloat162* hi,
-                             const __nv_bfloat162* lo, long long kp2, double2* out) {
+// rho [ng][nt] (FP64) or the three BF16 planes [ngp][kp] -> [nt][ng] double2
+__global__ void k_rho_export(int ng, long long nt, const double2* R64, const __nv_bfloat162* p0,
+                             long long plane2, long long kp2, double2* out) {
     const long long n = nt * ng;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -29,9 +29,11 @@ __global__ void k_rho_export(int ng, long long nt, const double2* R64, const __n
         if (R64) {
             out[i] = R64[(long long)g * nt + t];
         } else {
-            const float2 h = __bfloat1622float2(hi[(long long)g * kp2 + t]);
-            const float2 l = __bfloat1622float2(lo[(long long)g * kp2 + t]);
-            out[i] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+            const long long o = (long long)g * kp2 + t;
+            const float2 a = __bfloat1622float2(p0[o]);
+            const float2 b = __bfloat1622float2(p0[o + plane2]);
+            const float2 c = __bfloat1622float2(p0[o + 2 * plane2]);
+            out[i] = make_double2((double)a.x + (double)b.x + (double)c.x, (double)a.y + (double)b.y + (double)c.y);
         }
     }
 }
@@ -293,7 +295,7 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
     s.have_rho = s.have_eps = false;
     s.ng = ng;
     s.ngp = (ng + 15) / 16 * 16;
-    s.kp = (2 * nt + 63) / 64 * 64;
+    s.kp = (2 * nt + 63) / 64 * 64;   // K' = 2 nt padded to the 32-element stage (and 128-byte rows)
     CUDA_OR_FAIL(s.kappa.ensure(3 * sizeof(double) * ng), "alloc");
     CUDA_OR_FAIL(s.kappa32.ensure(3 * sizeof(float) * ng), "alloc");
     CUDA_OR_FAIL(s.vs.ensure(sizeof(double) * ng), "alloc");
@@ -304,7 +306,7 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
     if (prec == QCX_FP64) {
         CUDA_OR_FAIL(s.rho.ensure((size_t)ng * nt * sizeof(double2)), "alloc rho");
     } else {
-        const size_t bytes = 2 * (size_t)s.ngp * s.kp * sizeof(__nv_bfloat16);
+        const size_t bytes = 3 * (size_t)s.ngp * s.kp * sizeof(__nv_bfloat16);
         CUDA_OR_FAIL(s.rho.ensure(bytes), "alloc rho");
         CUDA_OR_FAIL(cudaMemsetAsync(s.rho.p, 0, bytes, ctx->stream), "clear rho");
     }
@@ -319,10 +321,9 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
             CUDA_OR_FAIL(ctx->scratch.ensure(nout), "alloc");
             dst = ctx->scratch.as<double2>();
         }
-        const __nv_bfloat162* hi = reinterpret_cast<const __nv_bfloat162*>(s.rho.p);
         k_rho_export<<<nblocks((size_t)nt * ng), 256, 0, ctx->stream>>>(
-            ng, nt, prec == QCX_FP64 ? s.rho.as<double2>() : nullptr, hi, hi + (size_t)s.ngp * (s.kp / 2), s.kp / 2,
-            dst);
+            ng, nt, prec == QCX_FP64 ? s.rho.as<double2>() : nullptr,
+            reinterpret_cast<const __nv_bfloat162*>(s.rho.p), (long long)s.ngp * (s.kp / 2), s.kp / 2, dst);
         CUDA_OR_FAIL(cudaGetLastError(), "export rho");
         if (dst != reinterpret_cast<double2*>(out_rho)) CUDA_OR_FAIL(qcx_copy_out(ctx, out_rho, dst, nout), "copy out");
     }

@@ -1,4 +1,546 @@
-// Mixed-precision chi0 on the tcgen05 tensor cores (placeholder until the kernel lands).
+// Mixed-precision chi0 (Eq. (RPA)) on the tcgen05 tensor cores with the Dyson
+// step fused in the epilogue.
+//
+// The complex contraction chi0_GG'(w) = pref sum_t W_t(w) conj(rho_t(G)) rho_t(G')
+// is one real GEMM per q,
+//   D[m][n] = sum_k A[m][k] B[n][k],   k = 2t + p (p = 0 real, 1 imaginary part),
+//   n = G,  m = (G'-block, w, re|im, G' in block),
+//   B[G][2t+p]           = (Re, Im) rho_t(G)                                 (operand read by TMA)
+//   A[(w,re,G')][2t+p]   = (Re, Im) (W_t(w) rho_t(G'))                      (generated in shared memory)
+//   A[(w,im,G')][2t+p]   = (Im, -Re)(W_t(w) rho_t(G')),
+// so the re rows of D hold Re chi0_GG' and the im rows Im chi0_GG'.  Both
+// operands are split into three BF16 terms x = x0 + x1 + x2 (x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)); D accumulates in FP32 the six
+// products whose order is at most 2, a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0,
+// so each product carries ~2^-24 relative error (the two-term split's 2^-16
+// is too coarse once the inverse amplifies it by the condition number of eps).
+// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is evaluated in FP64 (dE is
+// a difference of FP64 band energies) and rounded to FP32 when used.
+//
+// The tensor core's FP32 accumulation truncates, so long sums drift (about
+// 2^-24 of the running value per MMA, always toward zero).  The accumulator
+// is therefore restarted every K stage: TMEM holds two buffers used in turn,
+// the finished buffer is drained into FP32 registers (round to nearest), and
+// every FLUSH stages the register partials are added into an FP64 buffer
+// owned by the CTA.  The Dyson step runs in FP64 from that buffer.
+//
+// CTA work item: one 64-row G' block, one frequency (a 128 x N accumulator:
+// 64 re rows and 64 im rows), one N chunk of G.  Warp roles: warp 0 issues
+// TMA loads of the B tiles (and, when the G range is split, of the A-source
+// rows); warp 1 owns TMEM and issues the MMAs from one thread; warps 2-9 form
+// W and the A tiles, drain the accumulators and run the epilogue
+// (eps = delta - v^1/2 chi0 v^1/2).  Every wait is bounded: on timeout the
+// kernel records an error status, lets its own copies and MMAs finish, frees
+// TMEM and returns.
 #include "qcx_internal.h"
 
-cudaError_t qcx_launch_chi0_mixed(qcx_ctx*, QSlot&, int, double2*, int*) { return cudaErrorNotSupported; }
+#include <cuda.h>
+
+namespace {
+
+constexpr int NTHREADS = 320;
+constexpr int NSTAGE = 3;
+constexpr int KSTEP = 32;                 // BF16 K elements per stage = one 64-byte swizzle row
+constexpr int ROWB = 2 * KSTEP;           // bytes per operand row in shared memory
+constexpr int NPIECE = 3;                 // BF16 terms per operand
+constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
+constexpr int GBLK = 64;                  // G' rows per half tile
+constexpr int FLUSH = 128;                // stages between FP64 flushes of the register partials
+constexpr int MAXHALF = 96;               // columns of the accumulator one thread drains (n_tile/2)
+constexpr long long WAIT_LIMIT = 4000000000LL;  // clock cycles (~2 s)
+constexpr int SMEM_LIMIT = 232448;
+
+struct TcArgs {
+    int ng, nw, nv, nc;
+    long long nt;
+    int n_tile, n_gb, kstages, src_from_b;
+    uint32_t acc_off, tmem_cols;      // second TMEM buffer column, columns allocated
+    const double* Ek;
+    const double* Ekq;
+    const double* w;
+    double eta;
+    double pref;
+    const double* vs;
+    double* acc64;    // [grid][128][n_tile] FP64 partial sums, one region per CTA
+    float* eps_re;    // [nw][ng][ng], eps^T: row G', column G
+    float* eps_im;
+    double2* chi;     // optional [nw][ng][ng], row G, column G'
+    int* status;
+};
+
+// ------------------------------------------------------------------- PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait by one thread.  Returns false on timeout (which also raises
+// the CTA abort flag and the global status) or when another role aborted.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                          bool honour_abort = true) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (honour_abort && *abort_flag) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort_flag = 1;
+            atomicExch(status, 1);
+            return false;
+        }
+    }
+}
+// warp-uniform version: lane 0 waits, the result is broadcast
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, status) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 32 TMEM lanes x 8 columns of 32-bit data into 8 registers per thread (no wait)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading-dimension offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;     // stride between 8-row groups
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)4 << 61;              // 64-byte swizzle
+    return d;
+}
+// byte offset of the 16-byte chunk j of row r in a 64-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw64_off(int r, int j) {
+    return (uint32_t)r * ROWB + ((uint32_t)(j ^ ((r >> 1) & 3)) << 4);
+}
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both operands K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+// (a, b) -> three packed BF16 pairs with a = a0 + a1 + a2, b = b0 + b1 + b2
+__device__ __forceinline__ void split3(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    p0 = *reinterpret_cast<uint32_t*>(&h);
+    const float ra = a - hf.x, rb = b - hf.y;
+    __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+    const float2 mf = __bfloat1622float2(m);
+    p1 = *reinterpret_cast<uint32_t*>(&m);
+    p2 = pack_bf16(ra - mf.x, rb - mf.y);
+}
+__device__ __forceinline__ float2 bf2(uint32_t u) {
+    return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_chi0_tc(const __grid_constant__ CUtensorMap mb0, const __grid_constant__ CUtensorMap mb1,
+              const __grid_constant__ CUtensorMap mb2, const __grid_constant__ CUtensorMap ms0,
+              const __grid_constant__ CUtensorMap ms1, const __grid_constant__ CUtensorMap ms2, TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gb = blockIdx.x / a.nw, iw = blockIdx.x % a.nw;
+    const int n0 = blockIdx.y * a.n_tile;
+    const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;          // one B piece
+    const uint32_t spiece = (uint32_t)GBLK * ROWB;              // one A-source piece
+    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * spiece;
+    const uint32_t aoff = NPIECE * bbytes + sbytes;             // A pieces start here in a stage
+    const uint32_t stage_bytes = aoff + NPIECE * ATILE;
+    constexpr int TPS = KSTEP / 2;                              // transitions per stage
+    unsigned char* tail = base + NSTAGE * stage_bytes;
+    float2* Wbuf = reinterpret_cast<float2*>(tail);             // [NSTAGE][TPS]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tail + NSTAGE * TPS * sizeof(float2));
+    uint64_t* full_b = bars;                 // TMA landed
+    uint64_t* full_a = bars + NSTAGE;        // A tiles written (8 warps)
+    uint64_t* empty = bars + 2 * NSTAGE;     // MMAs of the stage done (smem reusable)
+    uint64_t* w_ready = bars + 3 * NSTAGE;   // W of the stage written (8 warps)
+    uint64_t* acc_full = bars + 4 * NSTAGE;  // [2] TMEM buffer holds a finished stage
+    uint64_t* drained = acc_full + 2;        // [2] TMEM buffer read out (8 warps)
+    uint64_t* mma_done = drained + 2;        // every issued MMA finished
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full_b[s], 1);
+            mbar_init(&full_a[s], 8);
+            mbar_init(&empty[s], 1);
+            mbar_init(&w_ready[s], 8);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&drained[b], 8);
+        }
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int last = -1;
+            for (int it = 0; it < a.kstages; ++it) {
+                const int s = it % NSTAGE;
+                const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status)) break;
+                unsigned char* st = base + s * stage_bytes;
+                mbar_arrive_tx(&full_b[s], NPIECE * bbytes + sbytes);
+                tma_load_2d(st, &mb0, &full_b[s], it * KSTEP, n0);
+                tma_load_2d(st + bbytes, &mb1, &full_b[s], it * KSTEP, n0);
+                tma_load_2d(st + 2 * bbytes, &mb2, &full_b[s], it * KSTEP, n0);
+                if (!a.src_from_b) {
+                    unsigned char* sp = st + NPIECE * bbytes;
+                    tma_load_2d(sp, &ms0, &full_b[s], it * KSTEP, gb * GBLK);
+                    tma_load_2d(sp + spiece, &ms1, &full_b[s], it * KSTEP, gb * GBLK);
+                    tma_load_2d(sp + 2 * spiece, &ms2, &full_b[s], it * KSTEP, gb * GBLK);
+                }
+                last = it;
+            }
+            // let the last copies land before the CTA can exit
+            if (last >= 0)
+                mbar_wait(&full_b[last % NSTAGE], (uint32_t)(last / NSTAGE) & 1u, abort_flag, a.status, false);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(128, a.n_tile);
+            for (int it = 0; it < a.kstages; ++it) {
+                const int s = it % NSTAGE;
+                const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+                const int b = it & 1;
+                if (!mbar_wait(&full_b[s], ph, abort_flag, a.status)) break;
+                if (!mbar_wait(&full_a[s], ph, abort_flag, a.status)) break;
+                if (it >= 2 && !mbar_wait(&drained[b], (uint32_t)((it - 2) >> 1) & 1u, abort_flag, a.status)) break;
+                tc_fence_after();
+                unsigned char* st = base + s * stage_bytes;
+                const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes, b2 = b1 + bbytes;
+                const uint32_t d = tmem + (uint32_t)b * a.acc_off;
+                const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE, a2 = a1 + ATILE;
+#pragma unroll
+                for (int kk = 0; kk < KSTEP / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, kk ? 1u : 0u);
+                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                    umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
+                    umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                    umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                }
+                umma_commit(&empty[s]);
+                umma_commit(&acc_full[b]);
+            }
+            // no MMA may still be running when TMEM is freed (also on the abort path)
+            umma_commit(mma_done);
+            mbar_wait(mma_done, 0, abort_flag, a.status, false);
+        }
+    } else {
+        // --------------------------------- A generation, accumulator drain, epilogue
+        const int wi = warp - 2;            // 0..7
+        const int g = threadIdx.x - 64;     // 0..255
+        const int j = g & 3;                // 16-byte chunk = 4 transitions
+        const int go = g >> 2;              // G' offset in the block (0..63)
+        const int Gp = gb * GBLK + go;
+        const int nvc = a.nv * a.nc;
+        // drain mapping: lane quadrant q, column half hc
+        const int q = warp & 3, hc = wi >> 2;
+        const int half = a.n_tile >> 1;
+        const int nch = half >> 3;          // 8-column chunks per thread
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int row = q * 32 + lane;      // accumulator row: 0..63 re, 64..127 im
+        double* acc64 = a.acc64 + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 + row) * a.n_tile + hc * half;
+        float part[MAXHALF];
+#pragma unroll
+        for (int i = 0; i < MAXHALF; ++i) part[i] = 0.0f;
+        bool ok = true;
+        int flushed = 0;                    // FP64 region initialised?
+
+        auto drain = [&](int itd) -> bool {
+            const int b = itd & 1;
+            if (!warp_wait(&acc_full[b], (uint32_t)(itd >> 1) & 1u, abort_flag, a.status)) return false;
+            tc_fence_after();
+            const uint32_t tb = tmem + lane_off + (uint32_t)b * a.acc_off + (uint32_t)(hc * half);
+#pragma unroll
+            for (int c = 0; c < MAXHALF / 8; ++c) {
+                if (c < nch) {
+                    uint32_t r[8];
+                    tmem_ld8(tb + (uint32_t)(c * 8), r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) part[c * 8 + i] += __uint_as_float(r[i]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&drained[b]);
+            if ((itd + 1) % FLUSH == 0 || itd + 1 == a.kstages) {
+#pragma unroll
+                for (int c = 0; c < MAXHALF / 8; ++c) {
+                    if (c < nch) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int col = c * 8 + i;
+                            acc64[col] = (flushed ? acc64[col] : 0.0) + (double)part[col];
+                            part[col] = 0.0f;
+                        }
+                    }
+                }
+                flushed = 1;
+            }
+            return true;
+        };
+
+        for (int it = 0; it < a.kstages && ok; ++it) {
+            const int s = it % NSTAGE;
+            const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+            if (!(ok = warp_wait(&empty[s], ph ^ 1u, abort_flag, a.status))) break;
+            // W_t(w) for the 16 transitions of this stage, 2 per warp, FP64
+            if (lane < 2) {
+                const int tl = wi * 2 + lane;
+                const long long t = (long long)it * TPS + tl;
+                float2 wt = make_float2(0.f, 0.f);
+                if (t < a.nt) {
+                    const long long k = t / nvc;
+                    const int rem = (int)(t - k * nvc);
+                    const int v = rem / a.nc, c = rem - v * a.nc;
+                    const double dE = a.Ekq[k * a.nc + c] - a.Ek[k * a.nv + v];
+                    const double om = a.w[iw];
+                    const double x1 = om - dE, x2 = om + dE;
+                    const double d1 = 1.0 / (x1 * x1 + a.eta * a.eta), d2 = 1.0 / (x2 * x2 + a.eta * a.eta);
+                    wt = make_float2((float)(x1 * d1 - x2 * d2), (float)(a.eta * (d2 - d1)));
+                }
+                Wbuf[s * TPS + tl] = wt;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&w_ready[s]);
+            if (!(ok = warp_wait(&w_ready[s], ph, abort_flag, a.status))) break;
+            if (!(ok = warp_wait(&full_b[s], ph, abort_flag, a.status))) break;
+            unsigned char* st = base + s * stage_bytes;
+            const unsigned char* srcb = a.src_from_b ? st : st + NPIECE * bbytes;
+            const uint32_t src_piece = a.src_from_b ? bbytes : spiece;
+            uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};   // re row
+            uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0}, im2[4] = {0, 0, 0, 0};   // im row
+            if (Gp < a.ng) {
+                const int srow = a.src_from_b ? Gp : go;
+                const uint32_t coff = sw64_off(srow, j);
+                const uint4 h0 = *reinterpret_cast<const uint4*>(srcb + coff);
+                const uint4 h1 = *reinterpret_cast<const uint4*>(srcb + src_piece + coff);
+                const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
+                const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
+                               v2[4] = {h2.x, h2.y, h2.z, h2.w};
+                const float2* Wv = Wbuf + s * TPS + 4 * j;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
+                    const float rr = f0.x + (f1.x + f2.x), ri = f0.y + (f1.y + f2.y);
+                    const float2 wq = Wv[qq];
+                    const float xr = wq.x * rr - wq.y * ri;
+                    const float xi = wq.x * ri + wq.y * rr;
+                    split3(xr, xi, re0[qq], re1[qq], re2[qq]);
+                    split3(xi, -xr, im0[qq], im1[qq], im2[qq]);
+                }
+            }
+            unsigned char* ap = st + aoff;
+            const uint32_t o_re = sw64_off(go, j), o_im = sw64_off(64 + go, j);
+            *reinterpret_cast<uint4*>(ap + o_re) = make_uint4(re0[0], re0[1], re0[2], re0[3]);
+            *reinterpret_cast<uint4*>(ap + ATILE + o_re) = make_uint4(re1[0], re1[1], re1[2], re1[3]);
+            *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_re) = make_uint4(re2[0], re2[1], re2[2], re2[3]);
+            *reinterpret_cast<uint4*>(ap + o_im) = make_uint4(im0[0], im0[1], im0[2], im0[3]);
+            *reinterpret_cast<uint4*>(ap + ATILE + o_im) = make_uint4(im1[0], im1[1], im1[2], im1[3]);
+            *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_im) = make_uint4(im2[0], im2[1], im2[2], im2[3]);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_a[s]);
+            if (it >= 1 && !(ok = drain(it - 1))) break;
+        }
+        if (ok) ok = drain(a.kstages - 1);
+        // -------------------------------------------------------------- epilogue
+        if (ok) {
+            const int cpart = row >> 6, gro = row & 63;
+            const int Gr = gb * GBLK + gro;
+            if (Gr < a.ng) {
+                const double vsp = a.vs[Gr];
+                const size_t rowoff = ((size_t)iw * a.ng + Gr) * a.ng;
+                float* plane = cpart ? a.eps_im : a.eps_re;
+                for (int col = 0; col < half; ++col) {
+                    const int G = n0 + hc * half + col;
+                    if (G < a.ng) {
+                        const double ch = a.pref * acc64[col];
+                        plane[rowoff + G] = (float)((cpart == 0 && G == Gr ? 1.0 : 0.0) - vsp * a.vs[G] * ch);
+                        if (a.chi) {
+                            double* dst = reinterpret_cast<double*>(a.chi + ((size_t)iw * a.ng + G) * a.ng + Gr);
+                            dst[cpart] = ch;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, a.tmem_cols);
+    }
+}
+
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled_t get_encode() {
+    static PFN_encodeTiled_t fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled_t>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows) {
+    PFN_encodeTiled_t enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)KSTEP, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, int* d_status) {
+    const int ng = s.ng;
+    const long long nt = (long long)ctx->nk * ctx->nv * ctx->nc;
+    TcArgs a{};
+    a.ng = ng;
+    a.nw = s.nw;
+    a.nv = ctx->nv;
+    a.nc = ctx->nc;
+    a.nt = nt;
+    int n_chunks;
+    if (s.ngp <= 2 * MAXHALF) {
+        n_chunks = 1;
+        a.n_tile = s.ngp;
+        a.src_from_b = 1;
+    } else {
+        n_chunks = (s.ngp + 2 * MAXHALF - 1) / (2 * MAXHALF);
+        a.n_tile = ((s.ngp + n_chunks - 1) / n_chunks + 15) / 16 * 16;
+        a.src_from_b = 0;
+    }
+    a.n_gb = (ng + GBLK - 1) / GBLK;
+    a.kstages = (int)(s.kp / KSTEP);
+    a.acc_off = a.n_tile <= 128 ? 128u : 256u;
+    a.tmem_cols = 2u * a.acc_off;
+    a.Ek = ctx->d_Ek.as<double>();
+    a.Ekq = ctx->d_Ekq.as<double>() + (size_t)iq * ctx->nk * ctx->nc;
+    a.w = s.w.as<double>();
+    a.eta = s.eta;
+    const double* L = ctx->lattice;
+    const double vol = fabs(L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                            L[2] * (L[3] * L[7] - L[4] * L[6]));
+    a.pref = 2.0 / (ctx->nk * vol);
+    a.vs = s.vs.as<double>();
+    a.eps_re = s.eps.as<float>();
+    a.eps_im = s.eps.as<float>() + (size_t)s.nw * ng * ng;
+    a.chi = chi;
+    a.status = d_status;
+    if (a.n_tile > 2 * MAXHALF || a.n_tile < 16) return cudaErrorNotSupported;
+
+    const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;
+    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * GBLK * ROWB;
+    const size_t stage_bytes = NPIECE * bbytes + sbytes + NPIECE * ATILE;
+    const size_t smem = 1024 + NSTAGE * stage_bytes + NSTAGE * (KSTEP / 2) * sizeof(float2) +
+                        (4 * NSTAGE + 5) * sizeof(uint64_t) + 16;
+    if (smem > SMEM_LIMIT) return cudaErrorNotSupported;
+
+    dim3 grid(a.n_gb * s.nw, n_chunks);
+    const size_t acc_bytes = (size_t)grid.x * grid.y * 128 * a.n_tile * sizeof(double);
+    cudaError_t e = s.acc64.ensure(acc_bytes);
+    if (e != cudaSuccess) return e;
+    a.acc64 = s.acc64.as<double>();
+
+    unsigned char* p0 = reinterpret_cast<unsigned char*>(s.rho.p);
+    const size_t plane = (size_t)s.ngp * s.kp * 2;
+    CUtensorMap mb[3], ms[3];
+    for (int i = 0; i < 3; ++i)
+        if (!make_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile) ||
+            !make_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK))
+            return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute((const void*)k_chi0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_chi0_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mb[0], mb[1], mb[2], ms[0], ms[1], ms[2], a);
+    return cudaGetLastError();
+}

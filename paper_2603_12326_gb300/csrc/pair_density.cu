@@ -45,8 +45,9 @@ template <typename T> struct PDArgs {
     const cplx<T>* Ck;       // [nk][nb][nv]
     const cplx<T>* Ckq;      // [nk][nb][nc]
     double2* R64;            // FP64 output [ng][nt]
-    __nv_bfloat162* Rhi;     // MIXED output planes [ngp][kp/2] (bf16 pairs re, im)
-    __nv_bfloat162* Rlo;
+    __nv_bfloat162* R0;      // MIXED output: three BF16 planes [ngp][kp/2] (pairs re, im),
+    __nv_bfloat162* R1;      // x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0),
+    __nv_bfloat162* R2;      // x2 = bf16(x - x0 - x1)
     long long kp2;           // row length of the bf16 planes in bf16x2 units
     cplx<T>* Sout;           // overlap mode: [nk][nb][nb]
 };
@@ -129,9 +130,11 @@ __device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T k
     }
 }
 
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+    p0 = __float2bfloat16_rn(x);
+    const float r = x - __bfloat162float(p0);
+    p1 = __float2bfloat16_rn(r);
+    p2 = __float2bfloat16_rn(r - __bfloat162float(p1));
 }
 
 template <typename T, int NCH>
@@ -178,11 +181,13 @@ __global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
             if (a.R64) {
                 a.R64[(long long)g * a.nt + t] = make_double2((double)acc.x, (double)acc.y);
             } else {
-                __nv_bfloat16 hr, lr, hi_, li;
-                split_bf16((float)acc.x, hr, lr);
-                split_bf16((float)acc.y, hi_, li);
-                a.Rhi[(long long)g * a.kp2 + t] = __halves2bfloat162(hr, hi_);
-                a.Rlo[(long long)g * a.kp2 + t] = __halves2bfloat162(lr, li);
+                __nv_bfloat16 r0, r1, r2, i0, i1, i2;
+                split3_bf16((float)acc.x, r0, r1, r2);
+                split3_bf16((float)acc.y, i0, i1, i2);
+                const long long o = (long long)g * a.kp2 + t;
+                a.R0[o] = __halves2bfloat162(r0, i0);
+                a.R1[o] = __halves2bfloat162(r1, i1);
+                a.R2[o] = __halves2bfloat162(r2, i2);
             }
         }
     }
@@ -480,8 +485,9 @@ cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precisio
     a.Ck = ctx->d_Ck32.as<float2>();
     a.Ckq = ctx->d_Ckq32.as<float2>() + (size_t)iq * ctx->nk * ctx->nb * ctx->nc;
     a.R64 = nullptr;
-    a.Rhi = reinterpret_cast<__nv_bfloat162*>(s.rho.p);
-    a.Rlo = a.Rhi + (size_t)s.ngp * (s.kp / 2);
+    a.R0 = reinterpret_cast<__nv_bfloat162*>(s.rho.p);
+    a.R1 = a.R0 + (size_t)s.ngp * (s.kp / 2);
+    a.R2 = a.R1 + (size_t)s.ngp * (s.kp / 2);
     a.kp2 = s.kp / 2;
     switch (ctx->nchar) {
         case 1: return launch_pd<float, 1>(ctx, a, smem, grid);

@@ -45,15 +45,16 @@ struct QSlot {
     DevBuf kappa32;            // [ng][3] float
     DevBuf vs;                 // [ng] double, sqrt(4 pi)/|q+G|
     DevBuf vs32;               // [ng] float
-    DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: hi and lo bf16 planes [ngp][kp]
+    DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: three bf16 planes [ngp][kp]
     DevBuf eps;                // FP64: [nw][ng][ng] double2 ; MIXED: re, im float planes [nw][ng][ng]
     DevBuf work;               // inverse work space
+    DevBuf acc64;              // FP64 partial sums of the tensor-core chi0 (one region per CTA)
     DevBuf w;                  // [nw] double
     DevBuf diag_inv;           // [nw][ng] double2
     DevBuf eps_diag;           // [nw][ng] double2
     DevBuf resid;              // [nw] double
     DevBuf flags;              // [nw] int (singular / error flags)
-    int ngp = 0;               // padded G rows of the bf16 planes
+    int ngp = 0;               // padded G rows of the bf16 planes (multiple of 16)
     long long kp = 0;          // padded K' = 2 nt columns of the bf16 planes
     double eta = 0.0;
 };

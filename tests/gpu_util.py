@@ -21,13 +21,17 @@ def rel(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
 
 
-def rel_masked(a, b, frac=1e-3):
-    """max relative error over entries with |b| > frac * max |b| (per leading index)."""
+def rel_spectrum(a, b, frac=1e-3):
+    """Loss tables [nw][ng]: for every spectrum L(w) at fixed G, the largest
+    relative error over the frequencies where L > frac * max_w L."""
     a = np.asarray(a)
     b = np.asarray(b)
     worst = 0.0
-    for i in range(b.shape[0]):
-        m = np.abs(b[i]) > frac * np.max(np.abs(b[i]))
-        if m.any():
-            worst = max(worst, float(np.max(np.abs(a[i][m] - b[i][m]) / np.abs(b[i][m]))))
+    for g in range(b.shape[1]):
+        col = b[:, g]
+        top = np.max(np.abs(col))
+        if top <= 0:
+            continue
+        m = np.abs(col) > frac * top
+        worst = max(worst, float(np.max(np.abs(a[m, g] - col[m]) / np.abs(col[m]))))
     return worst

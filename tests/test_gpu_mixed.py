@@ -1,0 +1,83 @@
+"""Mixed-precision GPU path (FP32 pair densities stored as BF16 hi/lo pairs,
+split-BF16 tcgen05 chi0 with FP32 accumulation, FP32 Gauss-Jordan inverse with
+an FP64 diagonal correction) vs the FP64 CPU oracle.
+
+Tolerances follow from the arithmetic: x = hi + lo in BF16 represents x to
+2^-16 (1.5e-5) relative; a product hi*hi + hi*lo + lo*hi misses at most
+3 * 2^-16 of |ab|; sums over transitions average these errors.  The loss
+functions must stay within 1e-4 relative wherever they exceed 1e-3 of their
+per-q maximum (the bar the method is held to)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import rpa
+from paper_2603_12326_gb300 import QCX_MIXED
+from tests.gpu_util import context, rel, rel_spectrum, set_oracle_states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = context()
+    yield c
+    c.close()
+
+
+def _run(ctx, j, p, want_chi=True):
+    rho = ctx.pair_density(j, p.G_int, QCX_MIXED, want=True)
+    chi = ctx.chi0(j, p.w, p.eta, QCX_MIXED, want=want_chi)
+    dinv, ed, resid = ctx.invert_eps(j, QCX_MIXED)
+    L1, L2 = ctx.loss_function(j, QCX_MIXED)
+    return rho, chi, dinv, ed, resid, L1, L2
+
+
+def _check(o, rho, chi, dinv, ed, L1, L2):
+    errs = {"rho": rel(rho, o["rho"]), "eps_diag": rel(ed, o["eps_diag"]),
+            "eps_inv_diag": rel(dinv, o["eps_inv_diag"]),
+            "L_lfe": rel_spectrum(L1, o["L_lfe"]), "L_nolfe": rel_spectrum(L2, o["L_nolfe"])}
+    if chi is not None:
+        errs["chi0"] = rel(chi, o["chi0"])
+    print("mixed-path errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs["rho"] < 5e-5
+    assert errs.get("chi0", 0.0) < 5e-5
+    assert errs["eps_diag"] < 5e-5
+    assert errs["eps_inv_diag"] < 1e-4
+    assert errs["L_lfe"] < 1e-4
+    assert errs["L_nolfe"] < 1e-4
+
+
+def test_small_workload_mixed(ctx):
+    p = synth.make_small()
+    iqs = [0, 4, 9]
+    refs = []
+    for iq in iqs:
+        Ck, Ckq = rpa.states(p, iq)
+        refs.append((Ck, Ckq, rpa.solve_q(p, iq, Ck, Ckq)))
+    set_oracle_states(ctx, p, iqs, refs[0][0], [r[1] for r in refs])
+    for j, (_, _, o) in enumerate(refs):
+        rho, chi, dinv, ed, resid, L1, L2 = _run(ctx, j, p)
+        _check(o, rho, chi, dinv, ed, L1, L2)
+
+
+def test_ragged_mixed_single_chunk(ctx):
+    """N_G = 13 (N tile 16, G' block partly empty), N_t = 120 (K padded to 256),
+    7 frequencies (the last frequency pair has one empty accumulator)."""
+    p = synth.make_tiny(shells_per_atom=3, n_k=2, nv=3, nc=5, ng=13, nq=1, nw=7)
+    Ck, Ckq = rpa.states(p, 0)
+    o = rpa.solve_q(p, 0, Ck, Ckq)
+    set_oracle_states(ctx, p, [0], Ck, [Ckq])
+    rho, chi, dinv, ed, resid, L1, L2 = _run(ctx, 0, p)
+    _check(o, rho, chi, dinv, ed, L1, L2)
+
+
+def test_split_g_range_mixed(ctx):
+    """N_G = 229 > 192: the G axis is split into N chunks and the A-operand rows
+    come from their own TMA tiles."""
+    p = synth.make_tiny(shells_per_atom=3, n_k=2, nv=2, nc=6, ng=229, nq=1, nw=5)
+    Ck, Ckq = rpa.states(p, 0)
+    o = rpa.solve_q(p, 0, Ck, Ckq)
+    set_oracle_states(ctx, p, [0], Ck, [Ckq])
+    rho, chi, dinv, ed, resid, L1, L2 = _run(ctx, 0, p)
+    _check(o, rho, chi, dinv, ed, L1, L2)
