@@ -1,0 +1,394 @@
+"""Benchmark: eps^-1 (q, w) blocks per second of the mixed-precision path.
+
+One step = the whole hot path over the mid-size workload (diamond cell,
+12 sp shells per atom -> N_b = 96, 8x8x8 k, N_v = 4, N_c = 32, N_t = 65536,
+N_G = 181, 50 q x 200 w = 10000 blocks): per q the pair densities, the
+tcgen05 chi0 with the Dyson step, the batched inverse and the loss tables;
+then the |q+G| binning of both loss functions and the FP64 halo rate and
+recoil spectrum.  Inputs (states) are resident in HBM before the timed
+region; the per-q R planes (150 MB) and states (1.3 GB) exceed the 129 MB
+L2, so no separate L2 flush is done.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank processes its own 50-q shard (weak scaling,
+no data-path collective); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eps^-1 (q,w) blocks/s vs FP64 plain GPU path at <=1e-4 rel err; tensor-pipe %"
+WORKLOAD = ("mid: diamond a=5.43 A, 12 sp shells/atom (N_b=96), 8x8x8 k, N_v=4, N_c=32 (N_t=65536), "
+            "N_G=181, 50 q x 200 w on 0-60 eV, eta=0.1 eV")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for i, n in enumerate(names):
+                    if r[5 + i].lower().startswith("active"):
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------- oracle arm
+def oracle_sample(prob, Ck, Ckq0, nk_sub=32, nw_sub=4):
+    """Time the CPU oracle on a bounded sample of one q: pair densities for
+    nk_sub of the k points and chi0 + eps + inverse + loss for nw_sub
+    frequencies over those transitions.  Returns (blocks/s extrapolated to
+    the full q, seconds spent, description)."""
+    from oracle import rpa
+    c, b = prob.cell, prob.basis
+    kap = prob.qpts[0][None, :] + prob.G_int @ c.recip
+    t0 = time.perf_counter()
+    rho = rpa.pair_density_lean(c.lattice, c.atoms, b.shell_atom, b.shell_l, b.shell_exp, prob.kpts[:nk_sub], kap,
+                                Ck[:nk_sub], Ckq0[:nk_sub])
+    t1 = time.perf_counter()
+    dE = rpa.transition_energies(prob.Ek[:nk_sub], prob.Ekq[0][:nk_sub])
+    ws = prob.w[np.linspace(1, len(prob.w) - 1, nw_sub).astype(int)]
+    W = rpa.transition_weights(dE, ws, prob.eta)
+    chi = rpa.chi0(rho, W, prob.nk, c.volume)
+    eps = rpa.dielectric_matrix(chi, rpa.coulomb_sqrt(prob.qpts[0], prob.G_int @ c.recip))
+    rpa.loss_functions(eps)
+    t2 = time.perf_counter()
+    scale = prob.nk / nk_sub
+    per_block = (t1 - t0) * scale / len(prob.w) + (t2 - t1) * scale / nw_sub
+    desc = (f"1 q of the mid workload: pair densities for {nk_sub}/{prob.nk} k points and chi0+eps+inverse+loss "
+            f"for {nw_sub}/{len(prob.w)} w over those transitions; time scaled linearly in k to all "
+            f"{prob.nk} k, pair densities amortised over {len(prob.w)} w")
+    return 1.0 / per_block, t2 - t0, desc
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle (the only implementation the paper gives
+    a definition for), timed on the host cores."""
+    if rank != 0:
+        return
+    import synth
+    from oracle import rpa
+    prob = synth.make_mid(nq=1)
+    Ck = rpa.orthonormalise(rpa.overlap(prob.cell.lattice, prob.cell.atoms, prob.basis.shell_atom,
+                                        prob.basis.shell_l, prob.basis.shell_exp, prob.kpts[:32]), prob.Zk[:32])
+    kq = prob.kpts[:32] + prob.qpts[0][None, :]
+    Ckq = rpa.orthonormalise(rpa.overlap(prob.cell.lattice, prob.cell.atoms, prob.basis.shell_atom,
+                                         prob.basis.shell_l, prob.basis.shell_exp, kq), prob.zkq(0)[:32])
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, _, desc = oracle_sample(prob, Ck, Ckq)
+        if i >= args.warmup:
+            vals.append(v)
+    v = float(np.median(vals))
+    out = {"metric": METRIC, "value": v, "unit": "blocks/s", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 10000 / v / 1.0,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": v, "unit": "blocks/s", "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": "blocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import synth
+    from paper_2603_12326_gb300 import QCX_FP64, QCX_MIXED, qcx, states
+    from paper_2603_12326_gb300.build import build
+
+    build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = qcx.Context(local, stream=stream.cuda_stream)
+    prob = synth.make_mid()
+    if ws > 1:   # weak scaling: each rank a different 50-q shard of the same distribution
+        prob = synth.make_mid_shard(rank)
+    nq, nw, ng = prob.nq, len(prob.w), prob.ng
+    Ck, Ckq = states.load_problem(ctx, prob)
+    G = prob.G_int
+    w = prob.w
+    eta = prob.eta
+    edges = np.linspace(0.0, 12.0, 121)          # |q+G| bins, bohr^-1
+    halo = qcx.halo_params()
+    nt = prob.nt
+    pref_flops = 8.0 * nt * ng * ng * nw          # algorithmic chi0 flops per q (one launch)
+
+    chi_events = []
+
+    def step(record=False):
+        for iq in range(nq):
+            ctx.pair_density(iq, G, QCX_MIXED)
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            ctx.chi0(iq, w, eta, QCX_MIXED)
+            if record:
+                e1.record(stream)
+                chi_events.append((e0, e1))
+            ctx.invert_eps(iq, QCX_MIXED, want=False)
+        Lb, cnt = ctx.bin_loss(list(range(nq)), 0, edges, nw)
+        Lb2, _ = ctx.bin_loss(list(range(nq)), 1, edges, nw)
+        nz = cnt > 0
+        qb = 0.5 * (edges[1:] + edges[:-1])[nz]
+        dR, dQ = ctx.rate(qb, w, Lb[nz], halo, nQ=10)
+        dR2, dQ2 = ctx.rate(qb, w, Lb2[nz], halo, nQ=10)
+        return dQ, dQ2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = _barrier_max(ws, ms)
+    blocks = nq * nw * args.steps * ws
+    value = blocks / (ms / 1e3)
+    chi_ms = [a.elapsed_time(b) for a, b in chi_events]
+    chi_avg = float(np.mean(chi_ms))
+    peaks = _peaks()
+    achieved = pref_flops / (chi_avg / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+
+    # ------------------------------------------------------ end to end (host buffers)
+    import ctypes as ct
+    pin = {}
+    for name, arr in (("kpts", prob.kpts), ("Ck", Ck), ("Ek", prob.Ek), ("qpts", prob.qpts), ("Ckq", Ckq),
+                      ("Ekq", prob.Ekq)):
+        t = torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()
+        pin[name] = t
+    outL = torch.empty((nq, 2, nw, ng), dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = outL.numel() * outL.element_size() + 2 * 10 * 8
+
+    def e2e_step():
+        st = qcx.qcx_set_states(ctx.h, prob.nk, qcx.P(pin["kpts"].data_ptr()), prob.nv, qcx.P(pin["Ck"].data_ptr()),
+                                qcx.P(pin["Ek"].data_ptr()), nq, qcx.P(pin["qpts"].data_ptr()), prob.nc,
+                                qcx.P(pin["Ckq"].data_ptr()), qcx.P(pin["Ekq"].data_ptr()))
+        ctx._check(st)
+        for iq in range(nq):
+            ctx.pair_density(iq, G, QCX_MIXED)
+            ctx.chi0(iq, w, eta, QCX_MIXED)
+            ctx.invert_eps(iq, QCX_MIXED, want=False)
+            ctx.loss_function(iq, QCX_MIXED, out_lfe=outL[iq, 0].numpy(), out_nolfe=outL[iq, 1].numpy())
+        Lb, cnt = ctx.bin_loss(list(range(nq)), 0, edges, nw)
+        nz = cnt > 0
+        ctx.rate(0.5 * (edges[1:] + edges[:-1])[nz], w, Lb[nz], halo, nQ=10)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_e2e = max(1, min(args.steps, 2))
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = _barrier_max(ws, e0.elapsed_time(e1) / n_e2e)
+
+    # -------------------------------------------------- FP64 plain GPU path (sample)
+    nw64 = 8
+    w64 = w[np.linspace(1, nw - 1, nw64).astype(int)]
+    ctx.pair_density(0, G, QCX_FP64)
+    ctx.chi0(0, w64, eta, QCX_FP64)
+    ctx.invert_eps(0, QCX_FP64, want=False)
+    torch.cuda.synchronize()
+    t = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t[0].record(stream)
+    ctx.pair_density(0, G, QCX_FP64)
+    t[1].record(stream)
+    ctx.chi0(0, w64, eta, QCX_FP64)
+    t[2].record(stream)
+    ctx.invert_eps(0, QCX_FP64, want=False)
+    t[3].record(stream)
+    torch.cuda.synchronize()
+    per_block64 = (t[0].elapsed_time(t[1]) / nw + t[1].elapsed_time(t[3]) / nw64) / 1e3
+    fp64_value = 1.0 / per_block64
+
+    # -------------------------------------------------------- CPU oracle (rank 0, N=1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, secs, desc = oracle_sample(prob, Ck, Ckq[0])
+        cpu = {"value": v, "unit": "blocks/s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
+               "seconds": round(secs, 2)}
+
+    if rank == 0:
+        launches_per_step = nq * 6 + 2 + 4       # per q: setup, pair density, chi0, GJ, refine, |q+G|; bins; rate
+        out = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "bf16",
+               "data": "synthetic (seeded states shaped like the paper's workloads)",
+               "config": {"workload": WORKLOAD, "blocks_per_step": nq * nw, "l2": "inputs larger than L2 (no flush)",
+                          "precision": "chi0 BF16 three-term split (6 products) with FP32 accumulation promoted "
+                                       "per K stage and FP64 partial sums; pair densities FP32; inverse FP32 + "
+                                       "FP64 diagonal correction; rate FP64",
+                          "parallelism": f"q shards x {ws}"},
+               "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "kernel": "k_chi0_tc", "flops_per_launch": pref_flops,
+                            "avg_launch_ms": chi_avg,
+                            "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)"},
+               "e2e": {"value": nq * nw * ws / (e2e_ms / 1e3), "unit": "blocks/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h},
+               "fp64_gpu": {"value": fp64_value, "unit": "blocks/s",
+                            "sample": f"1 q: FP64 pair densities amortised over {nw} w + FP64 chi0/inverse "
+                                      f"for {nw64} w"},
+               "speedup_vs_fp64_gpu": value / fp64_value,
+               "gpu_launches": launches_per_step * args.steps,
+               "clocks": clocks}
+        if cpu:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def run_profile_case():
+    """1 q x 50 w of the mid workload through the mixed path, twice."""
+    import torch
+
+    import synth
+    from paper_2603_12326_gb300 import QCX_MIXED, qcx, states
+    from paper_2603_12326_gb300.build import build
+    build()
+    ctx = qcx.Context(0)
+    prob = synth.make_mid(nq=1, nw=50)
+    states.load_problem(ctx, prob)
+    for _ in range(2):
+        ctx.pair_density(0, prob.G_int, QCX_MIXED)
+        ctx.chi0(0, prob.w, prob.eta, QCX_MIXED)
+        ctx.invert_eps(0, QCX_MIXED, want=False)
+    ctx.sync()
+    torch.cuda.synchronize()
+    ctx.close()
+    print("profile case done")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small case for profilers: 1 q x 50 w of the mid workload, 2 passes, no report")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.profile_case:
+        run_profile_case()
+    elif args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -243,6 +243,17 @@ def make_mid(nq: int | None = None, nw: int | None = None) -> Problem:
     return truncate(p, nq, nw)
 
 
+def make_mid_shard(shard: int) -> Problem:
+    """The mid workload with its own 50 q (and k+q states) for shard number
+    `shard` (weak scaling across processes); k states and basis are shared."""
+    p = make_mid()
+    rng = np.random.default_rng([1236, 7, shard])
+    p.qpts = random_q(rng, p.cell, 50, 4.0, p.G_int)
+    p.Ekq = band_energies(rng, (50, p.nk, p.nc), 1.1, 30.0)
+    p.q_index = np.arange(50) + 50 * (shard + 1)
+    return p
+
+
 def make_large(nq: int | None = None, nw: int | None = None) -> Problem:
     """Large all-electron-style workload (seed 1239).  The raw draws at k+q
     are [nq][1728][144][144] complex; ask for a few q only."""
