@@ -111,7 +111,7 @@ def _barrier(ws):
 
 
 # --------------------------------------------------------------- oracle arm
-def oracle_sample(prob, Ck, Ckq0, nk_sub=32, nw_sub=4):
+def oracle_sample(prob, Ck, Ckq0, nk_sub=128, nw_sub=4):
     """Time the CPU oracle on a bounded sample of one q: pair densities for
     nk_sub of the k points and chi0 + eps + inverse + loss for nw_sub
     frequencies over those transitions.  Returns (blocks/s extrapolated to
@@ -154,10 +154,10 @@ def run_reference(args, ws, rank):
     from oracle import rpa
     prob = synth.make_mid(nq=1)
     Ck = rpa.orthonormalise(rpa.overlap(prob.cell.lattice, prob.cell.atoms, prob.basis.shell_atom,
-                                        prob.basis.shell_l, prob.basis.shell_exp, prob.kpts[:32]), prob.Zk[:32])
-    kq = prob.kpts[:32] + prob.qpts[0][None, :]
+                                        prob.basis.shell_l, prob.basis.shell_exp, prob.kpts[:128]), prob.Zk[:128])
+    kq = prob.kpts[:128] + prob.qpts[0][None, :]
     Ckq = rpa.orthonormalise(rpa.overlap(prob.cell.lattice, prob.cell.atoms, prob.basis.shell_atom,
-                                         prob.basis.shell_l, prob.basis.shell_exp, kq), prob.zkq(0)[:32])
+                                         prob.basis.shell_l, prob.basis.shell_exp, kq), prob.zkq(0)[:128])
     vals = []
     for i in range(args.warmup + args.steps):
         v, _, desc = oracle_sample(prob, Ck, Ckq)

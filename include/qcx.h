@@ -58,9 +58,11 @@ typedef enum {
 
 typedef enum {
     QCX_FP64 = 0,   /* plain FP64 throughout                                                    */
-    QCX_MIXED = 1   /* FP32 pair densities, chi0 as split-BF16 (hi*hi + hi*lo + lo*hi) tcgen05
-                       products with FP32 accumulation, FP32 Gauss-Jordan inverse with an FP64
-                       residual correction; dE and W in FP64                                       */
+    QCX_MIXED = 1   /* FP32 pair densities kept as three BF16 terms; chi0 as three-term split-BF16
+                       tcgen05 products (the six of order <= 2) with the FP32 tensor-core sums
+                       promoted every two K stages and accumulated in FP64; eps stored in FP64;
+                       FP32 Gauss-Jordan inverse with an FP64 residual correction of the diagonal
+                       for ill-conditioned blocks (kappa_1 > 1e3); dE and w -+ dE in FP64       */
 } qcx_precision;
 
 typedef struct { double re, im; } qcx_c64;
@@ -164,12 +166,14 @@ qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, q
                     qcx_c64* out_chi0);
 
 /* Inverse of every eps(w) of the last qcx_chi0(iq) call: Gauss-Jordan with
- * partial pivoting (FP64, or FP32 followed by one FP64 residual correction
- * of the diagonal for QCX_MIXED).  Writes, if not NULL,
+ * partial pivoting (FP64; for QCX_MIXED FP32 followed, where the block is
+ * ill-conditioned, by one FP64 residual correction of the diagonal).
+ * Writes, if not NULL,
  *   out_diag_inv[nw][ng]   [eps^-1]_GG                     (Eq. (eps_LFE))
  *   out_eps_diag[nw][ng]   eps_GG                          (Eq. (eps_noLFE))
- *   out_resid[nw]          max_G |correction| / |[eps^-1]_GG| of the FP64
- *                          step (QCX_MIXED), 0 for QCX_FP64.
+ *   out_resid[nw]          QCX_MIXED: max_G |correction| / |[eps^-1]_GG| of the
+ *                          FP64 correction for blocks with kappa_1 > 1e3 (the
+ *                          ill-conditioned ones), 0 for the others; 0 for QCX_FP64.
  * and keeps the loss tables of iq in the context.
  * Errors: QCX_ERR_STATE, QCX_ERR_SINGULAR (zero pivot in some block; the
  * other blocks are valid), QCX_ERR_ALLOC, QCX_ERR_CUDA. */

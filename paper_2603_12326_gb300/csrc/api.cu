@@ -355,7 +355,7 @@ qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, q
     CUDA_OR_FAIL(s.w.ensure(sizeof(double) * nw), "alloc");
     CUDA_OR_FAIL(cudaMemcpyAsync(s.w.p, wh.data(), sizeof(double) * nw, cudaMemcpyHostToDevice, ctx->stream), "copy w");
     const size_t nmat = (size_t)nw * ng * ng;
-    CUDA_OR_FAIL(s.eps.ensure(nmat * (prec == QCX_FP64 ? sizeof(double2) : 2 * sizeof(float))), "alloc eps");
+    CUDA_OR_FAIL(s.eps.ensure(nmat * sizeof(double2)), "alloc eps");
     double2* chi = nullptr;
     if (out_chi0) {
         chi = qcx_is_device_ptr(out_chi0) ? reinterpret_cast<double2*>(out_chi0) : nullptr;

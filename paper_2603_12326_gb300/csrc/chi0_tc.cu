@@ -14,15 +14,16 @@
 // products whose order is at most 2, a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0,
 // so each product carries ~2^-24 relative error (the two-term split's 2^-16
 // is too coarse once the inverse amplifies it by the condition number of eps).
-// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is evaluated in FP64 (dE is
-// a difference of FP64 band energies) and rounded to FP32 when used.
+// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is tabulated per q by
+// k_weights with dE and w -+ dE in FP64 and fetched with each K stage.
 //
 // The tensor core's FP32 accumulation truncates, so long sums drift (about
 // 2^-24 of the running value per MMA, always toward zero).  The accumulator
-// is therefore restarted every K stage: TMEM holds two buffers used in turn,
-// the finished buffer is drained into FP32 registers (round to nearest), and
-// every FLUSH stages the register partials are added into an FP64 buffer
-// owned by the CTA.  The Dyson step runs in FP64 from that buffer.
+// is therefore restarted every PROMOTE K stages: TMEM holds two buffers used
+// in turn, the finished buffer is drained into FP32 registers (round to
+// nearest), and every FLUSH stages the register partials are added into an
+// FP64 buffer owned by the CTA.  The Dyson step runs in FP64 from that
+// buffer and eps is stored in FP64.
 //
 // CTA work item: one 64-row G' block, one frequency (a 128 x N accumulator:
 // 64 re rows and 64 im rows), one N chunk of G.  Warp roles: warp 0 issues
@@ -36,6 +37,8 @@
 
 #include <cuda.h>
 
+#include <algorithm>
+
 namespace {
 
 constexpr int NTHREADS = 320;
@@ -45,6 +48,7 @@ constexpr int ROWB = 2 * KSTEP;           // bytes per operand row in shared mem
 constexpr int NPIECE = 3;                 // BF16 terms per operand
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per half tile
+constexpr int PROMOTE = 2;                // K stages accumulated in one TMEM buffer
 constexpr int FLUSH = 128;                // stages between FP64 flushes of the register partials
 constexpr int MAXHALF = 96;               // columns of the accumulator one thread drains (n_tile/2)
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock cycles (~2 s)
@@ -55,15 +59,12 @@ struct TcArgs {
     long long nt;
     int n_tile, n_gb, kstages, src_from_b;
     uint32_t acc_off, tmem_cols;      // second TMEM buffer column, columns allocated
-    const double* Ek;
-    const double* Ekq;
-    const double* w;
-    double eta;
+    const float2* wtab;   // [nw][kp/2] W_t(w) in FP32 (tabulated with FP64 dE)
+    long long wld;        // row length of wtab
     double pref;
     const double* vs;
     double* acc64;    // [grid][128][n_tile] FP64 partial sums, one region per CTA
-    float* eps_re;    // [nw][ng][ng], eps^T: row G', column G
-    float* eps_im;
+    double2* eps;     // [nw][ng][ng], eps^T: row G', column G (FP64)
     double2* chi;     // optional [nw][ng][ng], row G, column G'
     int* status;
 };
@@ -122,6 +123,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
             "r"(smem_u32(dst)),
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
+}
+
+// plain bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -214,8 +223,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t* full_b = bars;                 // TMA landed
     uint64_t* full_a = bars + NSTAGE;        // A tiles written (8 warps)
     uint64_t* empty = bars + 2 * NSTAGE;     // MMAs of the stage done (smem reusable)
-    uint64_t* w_ready = bars + 3 * NSTAGE;   // W of the stage written (8 warps)
-    uint64_t* acc_full = bars + 4 * NSTAGE;  // [2] TMEM buffer holds a finished stage
+    uint64_t* acc_full = bars + 3 * NSTAGE;  // [2] TMEM buffer holds a finished window
     uint64_t* drained = acc_full + 2;        // [2] TMEM buffer read out (8 warps)
     uint64_t* mma_done = drained + 2;        // every issued MMA finished
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
@@ -226,7 +234,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&full_b[s], 1);
             mbar_init(&full_a[s], 8);
             mbar_init(&empty[s], 1);
-            mbar_init(&w_ready[s], 8);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -251,7 +258,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
                 if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status)) break;
                 unsigned char* st = base + s * stage_bytes;
-                mbar_arrive_tx(&full_b[s], NPIECE * bbytes + sbytes);
+                mbar_arrive_tx(&full_b[s], NPIECE * bbytes + sbytes + TPS * (uint32_t)sizeof(float2));
+                bulk_load(Wbuf + s * TPS, a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2),
+                          &full_b[s]);
                 tma_load_2d(st, &mb0, &full_b[s], it * KSTEP, n0);
                 tma_load_2d(st + bbytes, &mb1, &full_b[s], it * KSTEP, n0);
                 tma_load_2d(st + 2 * bbytes, &mb2, &full_b[s], it * KSTEP, n0);
@@ -274,10 +283,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int it = 0; it < a.kstages; ++it) {
                 const int s = it % NSTAGE;
                 const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
-                const int b = it & 1;
+                const int win = it / PROMOTE, b = win & 1;
+                const bool first = (it % PROMOTE) == 0;
+                const bool last = (it % PROMOTE) == PROMOTE - 1 || it + 1 == a.kstages;
                 if (!mbar_wait(&full_b[s], ph, abort_flag, a.status)) break;
                 if (!mbar_wait(&full_a[s], ph, abort_flag, a.status)) break;
-                if (it >= 2 && !mbar_wait(&drained[b], (uint32_t)((it - 2) >> 1) & 1u, abort_flag, a.status)) break;
+                if (first && win >= 2 &&
+                    !mbar_wait(&drained[b], (uint32_t)((win - 2) >> 1) & 1u, abort_flag, a.status))
+                    break;
                 tc_fence_after();
                 unsigned char* st = base + s * stage_bytes;
                 const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes, b2 = b1 + bbytes;
@@ -286,7 +299,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < KSTEP / 16; ++kk) {
                     const uint32_t off = kk * 32;
-                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, kk ? 1u : 0u);
+                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
                     umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
                     umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
                     umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
                 }
                 umma_commit(&empty[s]);
-                umma_commit(&acc_full[b]);
+                if (last) umma_commit(&acc_full[b]);
             }
             // no MMA may still be running when TMEM is freed (also on the abort path)
             umma_commit(mma_done);
@@ -307,48 +320,49 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int j = g & 3;                // 16-byte chunk = 4 transitions
         const int go = g >> 2;              // G' offset in the block (0..63)
         const int Gp = gb * GBLK + go;
-        const int nvc = a.nv * a.nc;
         // drain mapping: lane quadrant q, column half hc
         const int q = warp & 3, hc = wi >> 2;
         const int half = a.n_tile >> 1;
-        const int nch = half >> 3;          // 8-column chunks per thread
+        const int nch8 = half >> 3;         // 8-column TMEM loads per thread
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const int row = q * 32 + lane;      // accumulator row: 0..63 re, 64..127 im
         double* acc64 = a.acc64 + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 + row) * a.n_tile + hc * half;
+        const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
         float part[MAXHALF];
 #pragma unroll
         for (int i = 0; i < MAXHALF; ++i) part[i] = 0.0f;
         bool ok = true;
         int flushed = 0;                    // FP64 region initialised?
 
-        auto drain = [&](int itd) -> bool {
-            const int b = itd & 1;
-            if (!warp_wait(&acc_full[b], (uint32_t)(itd >> 1) & 1u, abort_flag, a.status)) return false;
+        auto drain = [&](int wd) -> bool {
+            const int b = wd & 1;
+            if (!warp_wait(&acc_full[b], (uint32_t)(wd >> 1) & 1u, abort_flag, a.status)) return false;
             tc_fence_after();
             const uint32_t tb = tmem + lane_off + (uint32_t)b * a.acc_off + (uint32_t)(hc * half);
+            // 8-column loads in pairs, one wait per pair (compile-time register indices)
 #pragma unroll
-            for (int c = 0; c < MAXHALF / 8; ++c) {
-                if (c < nch) {
-                    uint32_t r[8];
-                    tmem_ld8(tb + (uint32_t)(c * 8), r);
-                    tmem_wait_ld();
+            for (int grp = 0; grp < MAXHALF / 16; ++grp) {
+                uint32_t r[2][8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) part[c * 8 + i] += __uint_as_float(r[i]);
-                }
+                for (int u = 0; u < 2; ++u)
+                    if (grp * 2 + u < nch8) tmem_ld8(tb + (uint32_t)((grp * 2 + u) * 8), r[u]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (grp * 2 + u < nch8) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) part[(grp * 2 + u) * 8 + i] += __uint_as_float(r[u][i]);
+                    }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&drained[b]);
-            if ((itd + 1) % FLUSH == 0 || itd + 1 == a.kstages) {
+            if (((wd + 1) * PROMOTE) % FLUSH == 0 || wd + 1 == nwin) {
 #pragma unroll
-                for (int c = 0; c < MAXHALF / 8; ++c) {
-                    if (c < nch) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int col = c * 8 + i;
-                            acc64[col] = (flushed ? acc64[col] : 0.0) + (double)part[col];
-                            part[col] = 0.0f;
-                        }
+                for (int c = 0; c < MAXHALF; ++c) {
+                    if (c < half) {
+                        acc64[c] = (flushed ? acc64[c] : 0.0) + (double)part[c];
+                        part[c] = 0.0f;
                     }
                 }
                 flushed = 1;
@@ -360,26 +374,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int s = it % NSTAGE;
             const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
             if (!(ok = warp_wait(&empty[s], ph ^ 1u, abort_flag, a.status))) break;
-            // W_t(w) for the 16 transitions of this stage, 2 per warp, FP64
-            if (lane < 2) {
-                const int tl = wi * 2 + lane;
-                const long long t = (long long)it * TPS + tl;
-                float2 wt = make_float2(0.f, 0.f);
-                if (t < a.nt) {
-                    const long long k = t / nvc;
-                    const int rem = (int)(t - k * nvc);
-                    const int v = rem / a.nc, c = rem - v * a.nc;
-                    const double dE = a.Ekq[k * a.nc + c] - a.Ek[k * a.nv + v];
-                    const double om = a.w[iw];
-                    const double x1 = om - dE, x2 = om + dE;
-                    const double d1 = 1.0 / (x1 * x1 + a.eta * a.eta), d2 = 1.0 / (x2 * x2 + a.eta * a.eta);
-                    wt = make_float2((float)(x1 * d1 - x2 * d2), (float)(a.eta * (d2 - d1)));
-                }
-                Wbuf[s * TPS + tl] = wt;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&w_ready[s]);
-            if (!(ok = warp_wait(&w_ready[s], ph, abort_flag, a.status))) break;
             if (!(ok = warp_wait(&full_b[s], ph, abort_flag, a.status))) break;
             unsigned char* st = base + s * stage_bytes;
             const unsigned char* srcb = a.src_from_b ? st : st + NPIECE * bbytes;
@@ -394,7 +388,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
                 const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
                                v2[4] = {h2.x, h2.y, h2.z, h2.w};
-                const float2* Wv = Wbuf + s * TPS + 4 * j;
+                const float4* Wv4 = reinterpret_cast<const float4*>(Wbuf + s * TPS + 4 * j);
+                const float4 wa = Wv4[0], wb = Wv4[1];
+                const float2 Wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                                      make_float2(wb.z, wb.w)};
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
                     const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
@@ -417,9 +414,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_a[s]);
-            if (it >= 1 && !(ok = drain(it - 1))) break;
+            // drain the previous window once this window's first stage is queued
+            if (it % PROMOTE == 0 && it >= PROMOTE && !(ok = drain(it / PROMOTE - 1))) break;
         }
-        if (ok) ok = drain(a.kstages - 1);
+        if (ok) ok = drain(nwin - 1);
         // -------------------------------------------------------------- epilogue
         if (ok) {
             const int cpart = row >> 6, gro = row & 63;
@@ -427,12 +425,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (Gr < a.ng) {
                 const double vsp = a.vs[Gr];
                 const size_t rowoff = ((size_t)iw * a.ng + Gr) * a.ng;
-                float* plane = cpart ? a.eps_im : a.eps_re;
+                double* plane = reinterpret_cast<double*>(a.eps) + cpart;
                 for (int col = 0; col < half; ++col) {
                     const int G = n0 + hc * half + col;
                     if (G < a.ng) {
                         const double ch = a.pref * acc64[col];
-                        plane[rowoff + G] = (float)((cpart == 0 && G == Gr ? 1.0 : 0.0) - vsp * a.vs[G] * ch);
+                        plane[2 * (rowoff + G)] = (cpart == 0 && G == Gr ? 1.0 : 0.0) - vsp * a.vs[G] * ch;
                         if (a.chi) {
                             double* dst = reinterpret_cast<double*>(a.chi + ((size_t)iw * a.ng + G) * a.ng + Gr);
                             dst[cpart] = ch;
@@ -447,6 +445,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, a.tmem_cols);
+    }
+}
+
+// W[w][t] = 1/(w - dE + i eta) - 1/(w + dE + i eta), dE = E_c(k+q) - E_v(k), with dE and
+// w -+ dE formed in FP64; zero for padded t.
+__global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, const double* Ek, const double* Ekq,
+                          const double* w, double eta, float2* W) {
+    const long long n = (long long)nw * ld;
+    const int nvc = nv * nc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int iw = (int)(i / ld);
+        const long long t = i - (long long)iw * ld;
+        float2 v = make_float2(0.f, 0.f);
+        if (t < nt) {
+            const long long k = t / nvc;
+            const int rem = (int)(t - k * nvc);
+            const int vv = rem / nc, c = rem - vv * nc;
+            const double dE = Ekq[k * nc + c] - Ek[k * nv + vv];
+            const double x1 = w[iw] - dE, x2 = w[iw] + dE;
+            const double d1 = 1.0 / (x1 * x1 + eta * eta), d2 = 1.0 / (x2 * x2 + eta * eta);
+            v = make_float2((float)(x1 * d1 - x2 * d2), (float)(eta * (d2 - d1)));
+        }
+        W[i] = v;
     }
 }
 
@@ -504,17 +525,13 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     a.kstages = (int)(s.kp / KSTEP);
     a.acc_off = a.n_tile <= 128 ? 128u : 256u;
     a.tmem_cols = 2u * a.acc_off;
-    a.Ek = ctx->d_Ek.as<double>();
-    a.Ekq = ctx->d_Ekq.as<double>() + (size_t)iq * ctx->nk * ctx->nc;
-    a.w = s.w.as<double>();
-    a.eta = s.eta;
+    a.wld = s.kp / 2;
     const double* L = ctx->lattice;
     const double vol = fabs(L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
                             L[2] * (L[3] * L[7] - L[4] * L[6]));
     a.pref = 2.0 / (ctx->nk * vol);
     a.vs = s.vs.as<double>();
-    a.eps_re = s.eps.as<float>();
-    a.eps_im = s.eps.as<float>() + (size_t)s.nw * ng * ng;
+    a.eps = s.eps.as<double2>();
     a.chi = chi;
     a.status = d_status;
     if (a.n_tile > 2 * MAXHALF || a.n_tile < 16) return cudaErrorNotSupported;
@@ -523,12 +540,24 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * GBLK * ROWB;
     const size_t stage_bytes = NPIECE * bbytes + sbytes + NPIECE * ATILE;
     const size_t smem = 1024 + NSTAGE * stage_bytes + NSTAGE * (KSTEP / 2) * sizeof(float2) +
-                        (4 * NSTAGE + 5) * sizeof(uint64_t) + 16;
+                        (3 * NSTAGE + 5) * sizeof(uint64_t) + 16;
     if (smem > SMEM_LIMIT) return cudaErrorNotSupported;
 
+    // W table for this q (FP64 dE and w -+ dE, stored FP32)
+    cudaError_t e = s.wtab.ensure((size_t)s.nw * (s.kp / 2) * sizeof(float2));
+    if (e != cudaSuccess) return e;
+    {
+        const long long n = (long long)s.nw * (s.kp / 2);
+        k_weights<<<(int)std::min<long long>((n + 255) / 256, 8192), 256, 0, ctx->stream>>>(
+            s.nw, s.kp / 2, nt, ctx->nv, ctx->nc, ctx->d_Ek.as<double>(),
+            ctx->d_Ekq.as<double>() + (size_t)iq * ctx->nk * ctx->nc, s.w.as<double>(), s.eta, s.wtab.as<float2>());
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    a.wtab = s.wtab.as<float2>();
     dim3 grid(a.n_gb * s.nw, n_chunks);
     const size_t acc_bytes = (size_t)grid.x * grid.y * 128 * a.n_tile * sizeof(double);
-    cudaError_t e = s.acc64.ensure(acc_bytes);
+    e = s.acc64.ensure(acc_bytes);
     if (e != cudaSuccess) return e;
     a.acc64 = s.acc64.as<double>();
 

@@ -6,22 +6,25 @@
 // One CTA per (q, w) block runs Gauss-Jordan elimination with partial
 // (row) pivoting in place on a work copy of the matrix, then undoes the
 // column permutation.  The FP64 path does this in double.  The mixed path
-// does it in FP32 and then applies one FP64 correction of the diagonal:
-// with R = I - A X (computed in FP64 from the FP32 A and X, whose products
-// are exact in FP64), [A^-1]_jj = X_jj + (X R)_jj + O(|R|^2).
+// does it in FP32 on the rounded copy of the FP64 matrix and records the
+// condition estimate kappa_1 = |A|_1 |X|_1.  Blocks with kappa_1 above
+// KAPPA_REFINE (the ill-conditioned ones, near the plasmon) then get one FP64
+// correction of the diagonal against the FP64 matrix: with R = I - A X,
+// [A^-1]_jj = X_jj + (X R)_jj + O(|R|^2).  Below that bound the FP32
+// inverse of the rounded matrix already sits within ~1e-5 of the FP64 one.
 #include "qcx_internal.h"
 #include "cplx.cuh"
 
 namespace {
 
 constexpr int INV_THREADS = 512;
+constexpr double KAPPA_REFINE = 1.0e3;
 
 template <typename T> struct InvArgs {
     int ng, nw;
     const double2* eps64;      // FP64 input [nw][ng][ng]
-    const float* eps_re;       // FP32 planar input [nw][ng][ng]
-    const float* eps_im;
     cplx<T>* X;                // work [nw][ng][ng]
+    double* kappa;             // [nw] condition estimate (mixed path) or null
     double2* diag_inv;         // [nw][ng]
     double2* eps_diag;         // [nw][ng]
     double* L;                 // [2][nw][ng] (LFE, noLFE)
@@ -48,22 +51,36 @@ __global__ void __launch_bounds__(INV_THREADS) k_gauss_jordan(InvArgs<T> a, int 
     C* X = a.X + (size_t)b * n * n;
     // load the matrix; record eps_GG and the loss without local fields
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        C v;
-        if (a.eps64) {
-            const double2 z = a.eps64[(size_t)b * n * n + e];
-            v = mk<T>((T)z.x, (T)z.y);
-        } else {
-            v = mk<T>((T)a.eps_re[(size_t)b * n * n + e], (T)a.eps_im[(size_t)b * n * n + e]);
-        }
-        X[e] = v;
+        const double2 z = a.eps64[(size_t)b * n * n + e];
+        X[e] = mk<T>((T)z.x, (T)z.y);
         const int i = e / n;
         if (e == i * n + i) {
-            const double re = (double)v.x, im = (double)v.y;
+            const double re = z.x, im = z.y;
             a.eps_diag[(size_t)b * n + i] = make_double2(re, im);
             a.L[((size_t)a.nw + b) * n + i] = im / (re * re + im * im);
         }
     }
-    if (threadIdx.x == 0) s_bad = 0;
+    __shared__ double s_norm;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        s_norm = 0.0;
+    }
+    __syncthreads();
+    if (a.kappa) {
+        // |A|_1: largest column sum of |A_ij|
+        double best = 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            double cs = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double2 z = a.eps64[(size_t)b * n * n + (size_t)i * n + j];
+                cs += sqrt(z.x * z.x + z.y * z.y);
+            }
+            best = fmax(best, cs);
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(&s_norm), (unsigned long long)__double_as_longlong(best));
+    }
     __syncthreads();
 
     for (int k = 0; k < n; ++k) {
@@ -171,73 +188,86 @@ __global__ void __launch_bounds__(INV_THREADS) k_gauss_jordan(InvArgs<T> a, int 
         a.diag_inv[(size_t)b * n + j] = make_double2((double)z.x, (double)z.y);
         if (write_lfe) a.L[(size_t)b * n + j] = -(double)z.y;
     }
+    if (a.kappa) {
+        // |X|_1 of the computed inverse
+        __shared__ double s_xnorm;
+        if (threadIdx.x == 0) s_xnorm = 0.0;
+        __syncthreads();
+        double best = 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            double cs = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const C z = X[(size_t)i * n + j];
+                cs += sqrt((double)z.x * z.x + (double)z.y * z.y);
+            }
+            best = fmax(best, cs);
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(&s_xnorm), (unsigned long long)__double_as_longlong(best));
+        __syncthreads();
+        if (threadIdx.x == 0) a.kappa[b] = s_norm * s_xnorm;
+    }
 }
 
-// FP64 correction of the diagonal of X = A^-1 (A planar FP32, X FP32):
-//   d_j = X_jj + sum_k X_jk (delta_kj - sum_l A_kl X_lj).
-// One CTA per block; 32-column panels; each thread owns (row k, column j)
-// pairs of the panel and accumulates in FP64.
+// FP64 correction of the diagonal of X ~ A^-1 for the ill-conditioned blocks
+// (A FP64, X FP32):  d_j = X_jj + sum_k X_jk (delta_kj - sum_l A_kl X_lj).
+// Grid (block, 32-column panel).  Well-conditioned blocks keep X_jj.
 constexpr int RF_COLS = 32;
-__global__ void __launch_bounds__(256) k_refine_diag(int n, int nw, const float* eps_re, const float* eps_im,
-                                                     const float2* Xall, const int* flags, double2* diag_inv,
+__global__ void __launch_bounds__(256) k_refine_diag(int n, const double2* Aall, const float2* Xall,
+                                                     const int* flags, const double* kappa, double2* diag_inv,
                                                      double* L, double* resid) {
     __shared__ double2 s_d[RF_COLS];
-    __shared__ double s_rel[RF_COLS];
-    const int b = blockIdx.x;
-    if (flags[b]) {
-        if (threadIdx.x == 0) resid[b] = 0.0;
+    const int b = blockIdx.x, j0 = blockIdx.y * RF_COLS;
+    if (flags[b] || j0 >= n) return;
+    const float2* X = Xall + (size_t)b * n * n;
+    if (!(kappa[b] > KAPPA_REFINE)) {
+        if (threadIdx.x < RF_COLS && j0 + threadIdx.x < n) {
+            const int j = j0 + threadIdx.x;
+            const float2 x = X[(size_t)j * n + j];
+            diag_inv[(size_t)b * n + j] = make_double2((double)x.x, (double)x.y);
+            L[(size_t)b * n + j] = -(double)x.y;
+        }
         return;
     }
-    const float* Ar = eps_re + (size_t)b * n * n;
-    const float* Ai = eps_im + (size_t)b * n * n;
-    const float2* X = Xall + (size_t)b * n * n;
-    double worst = 0.0;
-    for (int j0 = 0; j0 < n; j0 += RF_COLS) {
-        if (threadIdx.x < RF_COLS) s_d[threadIdx.x] = make_double2(0.0, 0.0);
-        __syncthreads();
-        const int jl = threadIdx.x & (RF_COLS - 1);
-        const int j = j0 + jl;
-        double2 part = make_double2(0.0, 0.0);
-        if (j < n) {
-            for (int k = threadIdx.x / RF_COLS; k < n; k += blockDim.x / RF_COLS) {
-                // y = sum_l A_kl X_lj  (FP64)
-                double yr = 0.0, yi = 0.0;
-                for (int l = 0; l < n; ++l) {
-                    const double ar = Ar[(size_t)k * n + l], ai = Ai[(size_t)k * n + l];
-                    const float2 x = X[(size_t)l * n + j];
-                    yr = fma(ar, (double)x.x, yr);
-                    yr = fma(-ai, (double)x.y, yr);
-                    yi = fma(ar, (double)x.y, yi);
-                    yi = fma(ai, (double)x.x, yi);
-                }
-                const double rr = (k == j ? 1.0 : 0.0) - yr, ri = -yi;
-                const float2 xjk = X[(size_t)j * n + k];
-                part.x += (double)xjk.x * rr - (double)xjk.y * ri;
-                part.y += (double)xjk.x * ri + (double)xjk.y * rr;
+    const double2* A = Aall + (size_t)b * n * n;
+    if (threadIdx.x < RF_COLS) s_d[threadIdx.x] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const int jl = threadIdx.x & (RF_COLS - 1);
+    const int j = j0 + jl;
+    double2 part = make_double2(0.0, 0.0);
+    if (j < n) {
+        for (int k = threadIdx.x / RF_COLS; k < n; k += blockDim.x / RF_COLS) {
+            double yr = 0.0, yi = 0.0;          // sum_l A_kl X_lj in FP64
+            for (int l = 0; l < n; ++l) {
+                const double2 av = A[(size_t)k * n + l];
+                const float2 x = X[(size_t)l * n + j];
+                yr = fma(av.x, (double)x.x, yr);
+                yr = fma(-av.y, (double)x.y, yr);
+                yi = fma(av.x, (double)x.y, yi);
+                yi = fma(av.y, (double)x.x, yi);
             }
+            const double rr = (k == j ? 1.0 : 0.0) - yr, ri = -yi;
+            const float2 xjk = X[(size_t)j * n + k];
+            part.x += (double)xjk.x * rr - (double)xjk.y * ri;
+            part.y += (double)xjk.x * ri + (double)xjk.y * rr;
         }
-        atomicAdd(&s_d[jl].x, part.x);
-        atomicAdd(&s_d[jl].y, part.y);
-        __syncthreads();
-        if (threadIdx.x < RF_COLS && j0 + threadIdx.x < n) {
-            const int jj = j0 + threadIdx.x;
-            const float2 x = X[(size_t)jj * n + jj];
-            const double dr = (double)x.x + s_d[threadIdx.x].x, di = (double)x.y + s_d[threadIdx.x].y;
-            diag_inv[(size_t)b * n + jj] = make_double2(dr, di);
-            L[(size_t)b * n + jj] = -di;
-            const double mag = sqrt(dr * dr + di * di);
-            s_rel[threadIdx.x] = mag > 0 ? sqrt(s_d[threadIdx.x].x * s_d[threadIdx.x].x +
-                                                s_d[threadIdx.x].y * s_d[threadIdx.x].y) / mag
-                                         : 0.0;
-        } else if (threadIdx.x < RF_COLS) {
-            s_rel[threadIdx.x] = 0.0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0)
-            for (int c = 0; c < RF_COLS; ++c) worst = fmax(worst, s_rel[c]);
-        __syncthreads();
     }
-    if (threadIdx.x == 0) resid[b] = worst;
+    atomicAdd(&s_d[jl].x, part.x);
+    atomicAdd(&s_d[jl].y, part.y);
+    __syncthreads();
+    if (threadIdx.x < RF_COLS && j0 + threadIdx.x < n) {
+        const int jj = j0 + threadIdx.x;
+        const float2 x = X[(size_t)jj * n + jj];
+        const double dr = (double)x.x + s_d[threadIdx.x].x, di = (double)x.y + s_d[threadIdx.x].y;
+        diag_inv[(size_t)b * n + jj] = make_double2(dr, di);
+        L[(size_t)b * n + jj] = -di;
+        const double mag = sqrt(dr * dr + di * di);
+        const double rel = mag > 0 ? sqrt(s_d[threadIdx.x].x * s_d[threadIdx.x].x +
+                                          s_d[threadIdx.x].y * s_d[threadIdx.x].y) / mag
+                                   : 0.0;
+        atomicMax(reinterpret_cast<unsigned long long*>(resid + b), (unsigned long long)__double_as_longlong(rel));
+    }
 }
 
 }  // namespace
@@ -254,6 +284,7 @@ cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double
         a.eps_diag = s.eps_diag.as<double2>();
         a.L = d_loss_out;
         a.flags = s.flags.as<int>();
+        a.kappa = nullptr;
         const size_t smem = (size_t)n * 2 * sizeof(double2) + (size_t)n * 2 * sizeof(int);
         cudaError_t e = cudaFuncSetAttribute((const void*)k_gauss_jordan<double>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -266,21 +297,26 @@ cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double
     InvArgs<float> a{};
     a.ng = n;
     a.nw = s.nw;
-    a.eps_re = s.eps.as<float>();
-    a.eps_im = s.eps.as<float>() + (size_t)s.nw * n * n;
+    a.eps64 = s.eps.as<double2>();
     a.X = s.work.as<float2>();
+    cudaError_t e = s.kappa1.ensure(sizeof(double) * s.nw);
+    if (e != cudaSuccess) return e;
+    a.kappa = s.kappa1.as<double>();
     a.diag_inv = s.diag_inv.as<double2>();
     a.eps_diag = s.eps_diag.as<double2>();
     a.L = d_loss_out;
     a.flags = s.flags.as<int>();
     const size_t smem = (size_t)n * 2 * sizeof(float2) + (size_t)n * 2 * sizeof(int);
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_gauss_jordan<float>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute((const void*)k_gauss_jordan<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
     k_gauss_jordan<float><<<s.nw, INV_THREADS, smem, ctx->stream>>>(a, 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_refine_diag<<<s.nw, 256, 0, ctx->stream>>>(n, s.nw, a.eps_re, a.eps_im, a.X, a.flags, a.diag_inv,
-                                                  d_loss_out, s.resid.as<double>());
+    e = cudaMemsetAsync(s.resid.p, 0, sizeof(double) * s.nw, ctx->stream);
+    if (e != cudaSuccess) return e;
+    dim3 grid(s.nw, (n + RF_COLS - 1) / RF_COLS);
+    k_refine_diag<<<grid, 256, 0, ctx->stream>>>(n, a.eps64, a.X, a.flags, a.kappa, a.diag_inv, d_loss_out,
+                                                  s.resid.as<double>());
     return cudaGetLastError();
 }

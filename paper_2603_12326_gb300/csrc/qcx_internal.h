@@ -46,9 +46,11 @@ struct QSlot {
     DevBuf vs;                 // [ng] double, sqrt(4 pi)/|q+G|
     DevBuf vs32;               // [ng] float
     DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: three bf16 planes [ngp][kp]
-    DevBuf eps;                // FP64: [nw][ng][ng] double2 ; MIXED: re, im float planes [nw][ng][ng]
+    DevBuf eps;                // [nw][ng][ng] double2 (MIXED stores eps^T: row G', column G)
     DevBuf work;               // inverse work space
     DevBuf acc64;              // FP64 partial sums of the tensor-core chi0 (one region per CTA)
+    DevBuf wtab;               // [nw][kp/2] float2 transition weights of the mixed path
+    DevBuf kappa1;             // [nw] double condition estimates of the mixed inverse
     DevBuf w;                  // [nw] double
     DevBuf diag_inv;           // [nw][ng] double2
     DevBuf eps_diag;           // [nw][ng] double2
