@@ -414,9 +414,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_a[s]);
-            // drain the previous window once this window's first stage is queued
-            if (it % PROMOTE == 0 && it >= PROMOTE && !(ok = drain(it / PROMOTE - 1))) break;
+            // drain the previous window once this window's A tiles are all queued (its
+            // MMAs finished long ago, so the drain does not wait on the tensor pipe)
+            if (it % PROMOTE == PROMOTE - 1 && it >= PROMOTE && !(ok = drain(it / PROMOTE - 1))) break;
         }
+        if (ok && nwin >= 2 && (a.kstages - 1) % PROMOTE != PROMOTE - 1) ok = drain(nwin - 2);
         if (ok) ok = drain(nwin - 1);
         // -------------------------------------------------------------- epilogue
         if (ok) {
