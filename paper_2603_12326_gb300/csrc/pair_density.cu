@@ -14,7 +14,10 @@
 // (E(0,0) = 1, E(1,0) = PA + i kappa/2p, E(0,1) = PB + i kappa/2p,
 //  E(1,1) = PA PB + (PA + PB) i kappa/2p + 1/2p - kappa^2/4p^2 with
 //  PA = -(beta/p) d, PB = (alpha/p) d).
-// The contraction rho = C_kq^H B C_k runs in shared memory per (k, G).
+// Shells on the same centre with the same exponent (an s and a p shell) form
+// one group, so the one-dimensional sums are formed once per group pair and
+// give all 16 s/p components.  The contraction rho = C_kq^H B C_k runs in
+// shared memory per (k, G).
 #include "qcx_internal.h"
 #include "cplx.cuh"
 
@@ -26,15 +29,15 @@ constexpr int PD_THREADS = 256;
 constexpr double LATTICE_CUT = 46.0;   // Gaussian prefactors below e^-46 ~ 1e-20 are dropped
 
 template <typename T> struct PDArgs {
-    int nb, nv, nc, nk, ng, nt, ldB, nshell;
-    int row_s0[65];          // shell row blocks: shells [row_s0[i], row_s0[i+1])
+    int nb, nv, nc, nk, ng, nt, ldB, ngrp;
+    int row_s0[65];          // group row blocks: groups [row_s0[i], row_s0[i+1])
     int nblk;
     int max_rows;            // rows of the largest block (Bs holds max_rows * ldB entries)
     int g_per_cta;
     T h;
-    T charang[4][3];
-    const int* shell_l;
-    const int* shell_mu0;
+    T charre[4][3], charim[4][3];   // e^{2 pi i chi_x} per character and axis
+    const int* grp_mu0;      // first basis function of each group (ngrp + 1 entries)
+    const int* grp_mask;     // bit 0: has s, bit 1: has p
     const int* dir_off;      // [npair][3]
     const int* dir_cnt;
     const int* dir_nlo;
@@ -52,36 +55,50 @@ template <typename T> struct PDArgs {
     cplx<T>* Sout;           // overlap mode: [nk][nb][nb]
 };
 
-// One shell pair's block of B into shared memory (row offset row0).
+// z^n for integer n (|n| small) by repeated squaring
+template <typename C> __device__ __forceinline__ C cpow_int(C z, int n) {
+    C r;
+    r.x = 1;
+    r.y = 0;
+    int m = n < 0 ? -n : n;
+    C b = z;
+    while (m) {
+        if (m & 1) r = cmul(r, b);
+        b = cmul(b, b);
+        m >>= 1;
+    }
+    if (n < 0) r.y = -r.y;     // |z| = 1: z^-n = conj(z^n)
+    return r;
+}
+
+// One group pair's block of B into shared memory (row offset row0).
 template <typename T, int NCH>
 __device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T kk[3], const T kap[3], T k2,
                                            cplx<T>* Bs, int row0) {
     using C = cplx<T>;
-    const int sa = ip / a.nshell, sb = ip % a.nshell;
+    const int ga = ip / a.ngrp, gb = ip % a.ngrp;
     const T* par = a.par + (size_t)ip * 8;
     const T p = par[0], ap = par[1], bp = par[2], pref = par[3];
-    const int la = a.shell_l[sa], lb = a.shell_l[sb];
     const T inv2p = T(0.5) / p;
     T s, c;
     sincos_t(kap[0] * par[4] + kap[1] * par[5] + kap[2] * par[6], &s, &c);
     const T amp = pref * exp_t(-k2 * T(0.25) / p) / T(NCH);
     const C common = mk<T>(amp * c, amp * s);
 
-    C E[3][NCH][4];
+    C E[3][NCH][4];      // per axis and character: E(0,0), E(1,0), E(0,1), E(1,1)
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         const int di = ip * 3 + x;
         const int off = a.dir_off[di], cnt = a.dir_cnt[di], nlo = a.dir_nlo[di];
         const T theta = (kk[x] + bp * kap[x]) * a.h;
         const T tk = kap[x] * inv2p;
+        T zs, zc;
+        sincos_t(theta, &zs, &zc);
+        const C z = mk<T>(zc, zs);
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
-            const T phi = theta + a.charang[ch][x];
-            T zs, zc, ss, cc;
-            sincos_t(phi, &zs, &zc);
-            sincos_t(phi * T(nlo), &ss, &cc);
-            C zn = mk<T>(cc, ss);
-            const C z = mk<T>(zc, zs);
+            const C zch = ch ? cmul(z, mk<T>(a.charre[ch][x], a.charim[ch][x])) : z;
+            C zn = cpow_int(zch, nlo);
             C M0 = mk<T>(0, 0), M1 = mk<T>(0, 0), M2 = mk<T>(0, 0);
             for (int j = 0; j < cnt; ++j) {
                 const C wd = a.tab[off + j];
@@ -90,41 +107,39 @@ __device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T k
                 const C t1 = cscale(t0, wd.y);
                 M1 = cadd(M1, t1);
                 M2 = cadd(M2, cscale(t1, wd.y));
-                zn = cmul(zn, z);
+                zn = cmul(zn, zch);
             }
             const C itkM0 = mk<T>(-tk * M0.y, tk * M0.x);
             const C itkM1 = mk<T>(-tk * M1.y, tk * M1.x);
-            C e0 = M0;
-            C e1 = cadd(cscale(M1, -bp), itkM0);                       // E(1,0)
-            C e2 = cadd(cscale(M1, ap), itkM0);                        // E(0,1)
-            C e3 = cadd(cadd(cscale(M2, -ap * bp), cscale(itkM1, ap - bp)),
-                        cscale(M0, inv2p - tk * tk));                  // E(1,1)
-            // an s function on one side makes the l = 1 slots equal to the l = 0 ones,
-            // so the component loop below can index with compile-time selectors
-            if (!la) { e1 = e0; e3 = e2; }
-            if (!lb) { e2 = e0; e3 = e1; }
-            E[x][ch][0] = e0;
-            E[x][ch][1] = e1;
-            E[x][ch][2] = e2;
-            E[x][ch][3] = e3;
+            E[x][ch][0] = M0;
+            E[x][ch][1] = cadd(cscale(M1, -bp), itkM0);                       // E(1,0)
+            E[x][ch][2] = cadd(cscale(M1, ap), itkM0);                        // E(0,1)
+            E[x][ch][3] = cadd(cadd(cscale(M2, -ap * bp), cscale(itkM1, ap - bp)),
+                               cscale(M0, inv2p - tk * tk));                  // E(1,1)
         }
     }
-    const int na = la ? 3 : 1, nbn = lb ? 3 : 1;
-    const int mu0 = a.shell_mu0[sa] - row0, nu0 = a.shell_mu0[sb];
+    // components: 0 = s, 1..3 = p_x, p_y, p_z; present ones map to consecutive basis rows
+    const int ma = a.grp_mask[ga], mb = a.grp_mask[gb];
+    const int mu0 = a.grp_mu0[ga] - row0 - ((ma & 1) ? 0 : 1);
+    const int nu0 = a.grp_mu0[gb] - ((mb & 1) ? 0 : 1);
+    const T fa = T(2) * sqrt(ap * p), fb = T(2) * sqrt(bp * p);   // p normalisation 2 sqrt(alpha)
 #pragma unroll
-    for (int ia = 0; ia < 3; ++ia) {
+    for (int ca = 0; ca < 4; ++ca) {
 #pragma unroll
-        for (int ib = 0; ib < 3; ++ib) {
-            if (ia < na && ib < nbn) {
+        for (int cb = 0; cb < 4; ++cb) {
+            const bool oka = ca == 0 ? (ma & 1) : (ma & 2);
+            const bool okb = cb == 0 ? (mb & 1) : (mb & 2);
+            if (oka && okb) {
                 C val = mk<T>(0, 0);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
-                    C prod = E[0][ch][(ia == 0) + 2 * (ib == 0)];
-                    prod = cmul(prod, E[1][ch][(ia == 1) + 2 * (ib == 1)]);
-                    prod = cmul(prod, E[2][ch][(ia == 2) + 2 * (ib == 2)]);
+                    C prod = E[0][ch][(ca == 1) + 2 * (cb == 1)];
+                    prod = cmul(prod, E[1][ch][(ca == 2) + 2 * (cb == 2)]);
+                    prod = cmul(prod, E[2][ch][(ca == 3) + 2 * (cb == 3)]);
                     val = cadd(val, prod);
                 }
-                Bs[(mu0 + ia) * a.ldB + nu0 + ib] = cmul(common, val);
+                const T f = (ca ? fa : T(1)) * (cb ? fb : T(1));
+                Bs[(mu0 + ca) * a.ldB + nu0 + cb] = cscale(cmul(common, val), f);
             }
         }
     }
@@ -157,10 +172,10 @@ __global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
         const T k2 = kap[0] * kap[0] + kap[1] * kap[1] + kap[2] * kap[2];
         for (int blk = 0; blk < a.nblk; ++blk) {
             const int s0 = a.row_s0[blk], s1 = a.row_s0[blk + 1];
-            const int row0 = a.shell_mu0[s0];
-            const int row1 = s1 < a.nshell ? a.shell_mu0[s1] : a.nb;
+            const int row0 = a.grp_mu0[s0];
+            const int row1 = a.grp_mu0[s1];
             __syncthreads();  // Bs free, Cks staged
-            const int p0 = s0 * a.nshell, p1 = s1 * a.nshell;
+            const int p0 = s0 * a.ngrp, p1 = s1 * a.ngrp;
             for (int ip = p0 + threadIdx.x; ip < p1; ip += blockDim.x) pair_block<T, NCH>(a, ip, kk, kap, k2, Bs, row0);
             __syncthreads();
             const int rows = row1 - row0;
@@ -204,10 +219,10 @@ __global__ void __launch_bounds__(PD_THREADS) k_overlap(PDArgs<T> a) {
     const T kap[3] = {0, 0, 0};
     for (int blk = 0; blk < a.nblk; ++blk) {
         const int s0 = a.row_s0[blk], s1 = a.row_s0[blk + 1];
-        const int row0 = a.shell_mu0[s0];
-        const int row1 = s1 < a.nshell ? a.shell_mu0[s1] : a.nb;
+        const int row0 = a.grp_mu0[s0];
+        const int row1 = a.grp_mu0[s1];
         __syncthreads();
-        for (int ip = s0 * a.nshell + threadIdx.x; ip < s1 * a.nshell; ip += blockDim.x)
+        for (int ip = s0 * a.ngrp + threadIdx.x; ip < s1 * a.ngrp; ip += blockDim.x)
             pair_block<T, NCH>(a, ip, kk, kap, T(0), Bs, row0);
         __syncthreads();
         for (int i = threadIdx.x; i < (row1 - row0) * a.nb; i += blockDim.x) {
@@ -239,12 +254,15 @@ __global__ void k_qsetup(const int* G, int ng, double q0, double q1, double q2, 
 
 template <typename T> void fill_common(qcx_ctx* ctx, PDArgs<T>& a) {
     a.nb = ctx->nb;
-    a.nshell = ctx->nshell;
+    a.ngrp = ctx->ngrp;
     a.h = (T)ctx->h;
     for (int c = 0; c < 4; ++c)
-        for (int x = 0; x < 3; ++x) a.charang[c][x] = (T)(2.0 * M_PI * ctx->chars[c][x]);
-    a.shell_l = ctx->d_shell_l.as<int>();
-    a.shell_mu0 = ctx->d_shell_mu0.as<int>();
+        for (int x = 0; x < 3; ++x) {
+            a.charre[c][x] = (T)cos(2.0 * M_PI * ctx->chars[c][x]);
+            a.charim[c][x] = (T)sin(2.0 * M_PI * ctx->chars[c][x]);
+        }
+    a.grp_mu0 = ctx->d_grp_mu0.as<int>();
+    a.grp_mask = ctx->d_grp_mask.as<int>();
     const PairTables& pt = ctx->pairs;
     a.dir_off = pt.dir_off.as<int>();
     a.dir_cnt = pt.dir_cnt.as<int>();
@@ -262,10 +280,10 @@ template <typename T> int plan_blocks(qcx_ctx* ctx, PDArgs<T>& a, int nv, size_t
     a.ldB = ldB;
     int nblk = 0, s = 0, rows_max = 0;
     a.row_s0[0] = 0;
-    while (s < ctx->nshell) {
+    while (s < ctx->ngrp) {
         int rows = 0, e = s;
-        while (e < ctx->nshell) {
-            const int r = ctx->shell_l[e] ? 3 : 1;
+        while (e < ctx->ngrp) {
+            const int r = ctx->grp_mu0_h[e + 1] - ctx->grp_mu0_h[e];
             if (rows + r > (int)max_rows) break;
             rows += r;
             ++e;
@@ -354,28 +372,50 @@ qcx_status qcx_build_pair_tables(qcx_ctx* ctx) {
     ctx->h = h;
     ctx->nchar = m;
 
-    const int ns = ctx->nshell;
-    const int npair = ns * ns;
+    // groups: consecutive shells on the same atom with the same exponent (at most one s and one p)
+    std::vector<int> gfirst, gmask, gmu0;
+    int mu = 0;
+    for (int sh = 0; sh < ctx->nshell;) {
+        int mask = 0, e = sh;
+        while (e < ctx->nshell && ctx->shell_atom[e] == ctx->shell_atom[sh] &&
+               ctx->shell_exp[e] == ctx->shell_exp[sh] && !(mask & (1 << ctx->shell_l[e])) &&
+               (e == sh || ctx->shell_l[e] > ctx->shell_l[e - 1])) {
+            mask |= 1 << ctx->shell_l[e];
+            ++e;
+        }
+        gfirst.push_back(sh);
+        gmask.push_back(mask);
+        gmu0.push_back(mu);
+        mu += ((mask & 1) ? 1 : 0) + ((mask & 2) ? 3 : 0);
+        sh = e;
+    }
+    gmu0.push_back(mu);
+    const int ng_ = (int)gfirst.size();
+    ctx->ngrp = ng_;
+    ctx->grp_mu0_h = gmu0;
+    const int npair = ng_ * ng_;
     std::vector<int> dir_off(npair * 3), dir_cnt(npair * 3), dir_nlo(npair * 3);
     std::vector<double> par(npair * 8);
     std::vector<double2> tab;
-    for (int sa = 0; sa < ns; ++sa) {
+    for (int ga = 0; ga < ng_; ++ga) {
+        const int sa = gfirst[ga];
         const double al = ctx->shell_exp[sa];
         const double* A = &ctx->atom_xyz[3 * ctx->shell_atom[sa]];
-        const double na = pow(2.0 * al / M_PI, 0.75) * (ctx->shell_l[sa] ? 2.0 * sqrt(al) : 1.0);
-        for (int sb = 0; sb < ns; ++sb) {
+        const double na = pow(2.0 * al / M_PI, 0.75);      // the p factor 2 sqrt(a) is folded in below
+        for (int gb = 0; gb < ng_; ++gb) {
+            const int sb = gfirst[gb];
             const double be = ctx->shell_exp[sb];
             const double* B = &ctx->atom_xyz[3 * ctx->shell_atom[sb]];
-            const double nbn = pow(2.0 * be / M_PI, 0.75) * (ctx->shell_l[sb] ? 2.0 * sqrt(be) : 1.0);
-            const int ip = sa * ns + sb;
-            const double p = al + be, mu = al * be / p;
+            const double nbn = pow(2.0 * be / M_PI, 0.75);
+            const int ip = ga * ng_ + gb;
+            const double p = al + be, mu_ = al * be / p;
             par[ip * 8 + 0] = p;
             par[ip * 8 + 1] = al / p;
             par[ip * 8 + 2] = be / p;
             par[ip * 8 + 3] = na * nbn * pow(M_PI / p, 1.5);
             for (int x = 0; x < 3; ++x) par[ip * 8 + 4 + x] = (al * A[x] + be * B[x]) / p;
             par[ip * 8 + 7] = 0.0;
-            const double R = sqrt(LATTICE_CUT / mu);
+            const double R = sqrt(LATTICE_CUT / mu_);
             for (int x = 0; x < 3; ++x) {
                 const double D = A[x] - B[x];
                 const int nlo = (int)std::ceil((D - R) / h);
@@ -385,7 +425,7 @@ qcx_status qcx_build_pair_tables(qcx_ctx* ctx) {
                 int cnt = 0;
                 for (int n = nlo; n <= nhi; ++n) {
                     const double d = D - h * n;
-                    tab.push_back(make_double2(exp(-mu * d * d), d));
+                    tab.push_back(make_double2(exp(-mu_ * d * d), d));
                     ++cnt;
                 }
                 dir_cnt[ip * 3 + x] = cnt;
@@ -412,6 +452,8 @@ qcx_status qcx_build_pair_tables(qcx_ctx* ctx) {
     UP(pt.par32, par32, float)
     UP(pt.tab64, tab, double2)
     UP(pt.tab32, tab32, float2)
+    UP(ctx->d_grp_mu0, gmu0, int)
+    UP(ctx->d_grp_mask, gmask, int)
 #undef UP
     return QCX_OK;
 }

@@ -102,6 +102,9 @@ struct qcx_ctx {
     std::vector<int> shell_atom, shell_l, shell_mu0;
     std::vector<double> shell_exp;
     DevBuf d_shell_l, d_shell_mu0;
+    int ngrp = 0;                      // shell groups (same atom and exponent, s then p)
+    std::vector<int> grp_mu0_h;        // [ngrp + 1] first basis function of each group
+    DevBuf d_grp_mu0, d_grp_mask;
     PairTables pairs;
 
     // states
