@@ -206,6 +206,40 @@ qcx_status qcx_rate(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const d
                     const double* L, const qcx_halo_params* params, double* out_dRdw, int nQ,
                     double* out_dRQ);
 
+/* ------------------------------------------------------- no allocation */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they need the result: a framework
+ * that owns the device allocator and forbids other libraries from calling
+ * cudaMalloc (which also synchronises the device, something a latency-bound
+ * or graph-replayed pipeline cannot afford), or a process that reserved its
+ * whole memory budget at start-up.  It computes what qcx_invert_eps computes
+ * for QCX_FP64 (Gauss-Jordan with partial pivoting in FP64) for nb
+ * caller-owned dielectric matrices, and allocates nothing:
+ *   eps[nb][n][n]           device, complex FP64, row-major (row G, column G')
+ *   out_diag_inv[nb][n]     device: [eps^-1]_GG
+ *   out_L_lfe[nb][n]        device or NULL: -Im [eps^-1]_GG
+ *   out_L_nolfe[nb][n]      device or NULL: -Im (1/eps_GG)
+ *   out_singular[nb]        device or NULL: 1 where a zero pivot was met
+ *                           (that matrix's outputs are then zero), else 0
+ *   cuda_stream             stream to run on (NULL = legacy default stream)
+ * The only scratch is a fixed 16 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits: calls need
+ * nb * n * n * 16 bytes <= 16 MiB, otherwise QCX_ERR_ARG and nothing runs.
+ * The first call on a device resolves the array's address for that device
+ * (cudaGetSymbolAddress with the device current); make that first call before
+ * any stream capture.  Every call shares the array and leaves its last
+ * contents there; every element a call uses is written by that call first,
+ * so nothing needs clearing.  Calls that overlap on the GPU (on different
+ * streams, or from different threads) race on the array: serialise them.
+ * No cudaMalloc, cudaFree or allocating library routine is called.  The call
+ * is asynchronous on cuda_stream.
+ * Errors: QCX_ERR_ARG (sizes, a non-device pointer, over the scratch limit),
+ * QCX_ERR_CUDA (no usable device, launch failure). */
+qcx_status qcx_eps_inverse_diag_noalloc(const qcx_c64* eps, int nb, int n, qcx_c64* out_diag_inv,
+                                        double* out_L_lfe, double* out_L_nolfe, int* out_singular,
+                                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,7 @@ _SIGS = {
     "qcx_loss_function": (I, [P, I, P, P]),
     "qcx_bin_loss": (I, [P, I, P, I, I, P, P, P]),
     "qcx_rate": (I, [P, I, P, I, P, P, ct.POINTER(HaloParams), P, I, P]),
+    "qcx_eps_inverse_diag_noalloc": (I, [P, I, I, P, P, P, P, P]),
 }
 
 
