@@ -307,6 +307,67 @@ def solve_q(problem, iq, Ck=None, Ckq=None, w=None):
 
 
 # --------------------------------------------------------------------------
+# uneven instances: one (q, w) block each, G set {G : |q+G| < G_max}
+# --------------------------------------------------------------------------
+def g_ball(recip, q, gmax):
+    """Integer G (rows of `recip` as basis) with |q + G| < gmax, in the order
+    of a plain scan over a bounding box (any order serves: the head is found
+    by its value G = 0)."""
+    recip = np.asarray(recip, float)
+    # |n_i| = |a_i . G| / (2 pi) <= |a_i| |G| / (2 pi), |G| < gmax + |q|
+    lat = 2.0 * np.pi * np.linalg.inv(recip).T
+    reach = gmax + np.linalg.norm(q)
+    m = [int(np.ceil(np.linalg.norm(lat[i]) * reach / (2.0 * np.pi))) + 1 for i in range(3)]
+    out = []
+    for n1 in range(-m[0], m[0] + 1):
+        for n2 in range(-m[1], m[1] + 1):
+            for n3 in range(-m[2], m[2] + 1):
+                k = np.asarray(q) + n1 * recip[0] + n2 * recip[1] + n3 * recip[2]
+                if np.dot(k, k) < gmax * gmax:
+                    out.append((n1, n2, n3))
+    return np.array(out, dtype=np.int64).reshape(-1, 3)
+
+
+def solve_instances(problem, inst_q, inst_w, inst_gmax, states_by_q):
+    """Heads of the loss functions of independent (q, w) blocks whose G sets
+    are {G : |q+G| < G_max} (uneven sizes): per instance the steps of
+    `solve_q` (Eq. (RPA), the Dyson step, Eqs. (eps_LFE), (eps_noLFE)) for one
+    frequency, returning L_LFE = -Im [eps^{-1}]_{00} and L_noLFE =
+    -Im (1/eps_00) at the head G = 0, and N_G.  Pair densities are formed once
+    per q on the largest of that q's G sets and restricted by G value.
+    states_by_q: {iq: (Ck, Ckq)}."""
+    c = problem.cell
+    b = problem.basis
+    inst_q = np.asarray(inst_q)
+    n = inst_q.shape[0]
+    L1 = np.empty(n)
+    L2 = np.empty(n)
+    ngs = np.empty(n, dtype=np.int64)
+    for iq in np.unique(inst_q):
+        sel = np.nonzero(inst_q == iq)[0]
+        q = problem.qpts[iq]
+        Ck, Ckq = states_by_q[int(iq)]
+        Gu = g_ball(c.recip, q, float(np.max(np.asarray(inst_gmax)[sel])))
+        col = {tuple(g): j for j, g in enumerate(Gu)}
+        kappa = q[None, :] + Gu @ c.recip
+        rho_u = pair_density_lean(c.lattice, c.atoms, b.shell_atom, b.shell_l, b.shell_exp,
+                                  problem.kpts, kappa, Ck, Ckq)
+        dE = transition_energies(problem.Ek, problem.Ekq[iq])
+        for i in sel:
+            Gi = g_ball(c.recip, q, float(inst_gmax[i]))
+            cols = np.array([col[tuple(g)] for g in Gi])
+            head = int(np.nonzero(np.all(Gi == 0, axis=1))[0][0])
+            W = transition_weights(dE, [inst_w[i]], problem.eta)
+            chi = chi0(rho_u[:, cols], W, problem.nk, c.volume)
+            eps = dielectric_matrix(chi, coulomb_sqrt(q, Gi @ c.recip))
+            Lf, Ln, _, _ = loss_functions(eps)
+            L1[i] = Lf[0, head]
+            L2[i] = Ln[0, head]
+            ngs[i] = Gi.shape[0]
+    return L1, L2, ngs
+
+
+# --------------------------------------------------------------------------
 # kinetic matrix (for the f-sum check only)
 # --------------------------------------------------------------------------
 def _gauss_moment(n, p):
