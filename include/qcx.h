@@ -206,6 +206,54 @@ qcx_status qcx_rate(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const d
                     const double* L, const qcx_halo_params* params, double* out_dRdw, int nQ,
                     double* out_dRQ);
 
+/* --------------------------------------------------- batched instances */
+
+/* Uneven (q, w) instances in one call: instance i is the frequency
+ * inst_w[i] (Hartree) of the q point inst_q[i] (an index into the q list of
+ * qcx_set_states) with its own G set {G : |q + G| < inst_gmax[i]} (bohr^-1),
+ * and yields the heads of the loss functions (Eq. (RPA) with the Dyson step;
+ * Eq. (eps_LFE) and Eq. (eps_noLFE) at G = 0):
+ *   out_L_lfe_head[i]   = -Im [eps^-1]_{00}
+ *   out_L_nolfe_head[i] = -Im (1 / eps_00)
+ *   out_ng[i]           = N_G of the instance (may be NULL).
+ * eta (Hartree) is shared.  QCX_FP64 computes everything in FP64; QCX_MIXED
+ * forms chi0 on the tensor cores (three-term BF16 split, FP32 accumulation
+ * promoted to FP64, eps in FP64), factors eps in FP32 (LU, partial pivoting)
+ * and refines the head with two FP64-residual correction steps.
+ * The first call with a new instance list (same q indices, cutoffs, eta and
+ * precision) plans the batch: G sets, pair densities once per distinct q on
+ * the union of its instances' sets, tile and per-SM instance lists; for
+ * QCX_MIXED it also times one CUDA graph per tile width and keeps the fastest
+ * (see qcx_batch_autotune).  The whole batch then runs as one captured CUDA
+ * graph (a single persistent tensor-core launch per 16 distinct q), replayed
+ * by later calls with the same list; only the frequencies may change between
+ * them.  The plan holds its own device buffers until the next plan, new
+ * states or qcx_destroy.  Inputs: host or device pointers; outputs: host or
+ * device pointers (the call synchronises the context stream).
+ * Errors: QCX_ERR_STATE (no states), QCX_ERR_ARG (sizes, q index, non-finite
+ * or non-positive cutoff, or G = 0 outside an instance's cutoff),
+ * QCX_ERR_UNSUPPORTED (an instance with N_G > 512), QCX_ERR_SINGULAR (zero
+ * pivot: that instance's L_LFE is 0), QCX_ERR_NOT_CONVERGED (QCX_MIXED: the
+ * last correction exceeded 1e-6 relative), QCX_ERR_TIMEOUT (a bounded wait in
+ * the tensor-core kernel gave up; results invalid), QCX_ERR_ALLOC,
+ * QCX_ERR_CUDA.  Outputs are written in every case except ARG, STATE,
+ * UNSUPPORTED, ALLOC and CUDA errors. */
+qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const double* inst_w,
+                           const double* inst_gmax, double eta, qcx_precision prec, double* out_L_lfe_head,
+                           double* out_L_nolfe_head, int* out_ng);
+
+/* Facts about the current batch plan, written to out[0 .. n-1] (host):
+ * [0] tile width cap (columns of G per tensor-core tile), [1] tiles,
+ * [2] persistent tensor-core CTAs, [3] solve CTAs, [4] kernels per replay,
+ * [5] 1 if the tile width was autotuned, [6] distinct q, [7] largest N_G,
+ * [8] autotuning time (microseconds), [9] precision.  Entries past 9 are 0.
+ * Errors: QCX_ERR_ARG, QCX_ERR_STATE (no plan yet; out is zeroed). */
+qcx_status qcx_batch_info(const qcx_ctx* ctx, int n, long long* out);
+
+/* Turn the tile-width autotuning of new QCX_MIXED batch plans on (default)
+ * or off (then the widest tiles are used).  Errors: QCX_ERR_ARG (ctx NULL). */
+qcx_status qcx_batch_autotune(qcx_ctx* ctx, int enable);
+
 /* ------------------------------------------------------- no allocation */
 
 /* The paper has no counterpart to this entry point; it exists for callers

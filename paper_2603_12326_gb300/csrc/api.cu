@@ -82,6 +82,7 @@ template <typename T> cudaError_t fetch(qcx_ctx* ctx, std::vector<T>& out, const
 }  // namespace
 
 qcx_ctx::~qcx_ctx() {
+    qcx_batch_destroy(batch);
     for (auto* l : loss) delete l;
     if (own_stream && stream) cudaStreamDestroy(stream);
 }
@@ -190,6 +191,7 @@ qcx_status qcx_set_basis(qcx_ctx* ctx, const double* lattice, int natom, const d
         nb += sl[s] ? 3 : 1;
     }
     // drop states that belonged to an earlier basis
+    ++ctx->gen;
     ctx->nk = ctx->nv = ctx->nc = ctx->nq = 0;
     for (auto& s : ctx->slot) {
         s.iq = -1;
@@ -268,6 +270,7 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
     k_to_float2<<<nblocks(nCk), 256, 0, ctx->stream>>>(ctx->d_Ck64.as<double2>(), ctx->d_Ck32.as<float2>(), nCk);
     k_to_float2<<<nblocks(nCkq), 256, 0, ctx->stream>>>(ctx->d_Ckq64.as<double2>(), ctx->d_Ckq32.as<float2>(), nCkq);
     CUDA_OR_FAIL(cudaGetLastError(), "convert states");
+    ++ctx->gen;
     ctx->nk = nk;
     ctx->nv = nv;
     ctx->nc = nc;

@@ -34,8 +34,7 @@
 // kernel records an error status, lets its own copies and MMAs finish, frees
 // TMEM and returns.
 #include "qcx_internal.h"
-
-#include <cuda.h>
+#include "tc_ptx.cuh"
 
 #include <algorithm>
 
@@ -43,15 +42,12 @@ namespace {
 
 constexpr int NTHREADS = 320;
 constexpr int NSTAGE = 3;
-constexpr int KSTEP = 32;                 // BF16 K elements per stage = one 64-byte swizzle row
-constexpr int ROWB = 2 * KSTEP;           // bytes per operand row in shared memory
 constexpr int NPIECE = 3;                 // BF16 terms per operand
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per half tile
 constexpr int PROMOTE = 2;                // K stages accumulated in one TMEM buffer
 constexpr int FLUSH = 128;                // stages between FP64 flushes of the register partials
 constexpr int MAXHALF = 96;               // columns of the accumulator one thread drains (n_tile/2)
-constexpr long long WAIT_LIMIT = 4000000000LL;  // clock cycles (~2 s)
 constexpr int SMEM_LIMIT = 232448;
 
 struct TcArgs {
@@ -68,139 +64,6 @@ struct TcArgs {
     double2* chi;     // optional [nw][ng][ng], row G, column G'
     int* status;
 };
-
-// ------------------------------------------------------------------- PTX
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait by one thread.  Returns false on timeout (which also raises
-// the CTA abort flag and the global status) or when another role aborted.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
-                          bool honour_abort = true) {
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (honour_abort && *abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
-            *abort_flag = 1;
-            atomicExch(status, 1);
-            return false;
-        }
-    }
-}
-// warp-uniform version: lane 0 waits, the result is broadcast
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, status) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
-            "r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-// plain bulk copy global -> shared (16-byte aligned, size a multiple of 16)
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-// 32 TMEM lanes x 8 columns of 32-bit data into 8 registers per thread (no wait)
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;              // leading-dimension offset (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;     // stride between 8-row groups
-    d |= (uint64_t)1 << 46;              // descriptor version
-    d |= (uint64_t)4 << 61;              // 64-byte swizzle
-    return d;
-}
-// byte offset of the 16-byte chunk j of row r in a 64-byte-swizzled K-major tile
-__device__ __forceinline__ uint32_t sw64_off(int r, int j) {
-    return (uint32_t)r * ROWB + ((uint32_t)(j ^ ((r >> 1) & 3)) << 4);
-}
-// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both operands K-major
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
-// (a, b) -> three packed BF16 pairs with a = a0 + a1 + a2, b = b0 + b1 + b2
-__device__ __forceinline__ void split3(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    p0 = *reinterpret_cast<uint32_t*>(&h);
-    const float ra = a - hf.x, rb = b - hf.y;
-    __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
-    const float2 mf = __bfloat1622float2(m);
-    p1 = *reinterpret_cast<uint32_t*>(&m);
-    p2 = pack_bf16(ra - mf.x, rb - mf.y);
-}
-__device__ __forceinline__ float2 bf2(uint32_t u) {
-    return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
-}
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_chi0_tc(const __grid_constant__ CUtensorMap mb0, const __grid_constant__ CUtensorMap mb1,
@@ -473,11 +336,13 @@ __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, co
     }
 }
 
+}  // namespace
+
 typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-PFN_encodeTiled_t get_encode() {
+static PFN_encodeTiled_t get_encode() {
     static PFN_encodeTiled_t fn = nullptr;
     if (!fn) {
         void* p = nullptr;
@@ -490,7 +355,7 @@ PFN_encodeTiled_t get_encode() {
     return fn;
 }
 
-bool make_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows) {
+bool qcx_make_bf16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows) {
     PFN_encodeTiled_t enc = get_encode();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
@@ -501,8 +366,6 @@ bool make_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows) 
                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, int* d_status) {
     const int ng = s.ng;
@@ -567,8 +430,8 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     const size_t plane = (size_t)s.ngp * s.kp * 2;
     CUtensorMap mb[3], ms[3];
     for (int i = 0; i < 3; ++i)
-        if (!make_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile) ||
-            !make_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK))
+        if (!qcx_make_bf16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile) ||
+            !qcx_make_bf16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK))
             return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute((const void*)k_chi0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -1,6 +1,7 @@
 // Internal declarations of libqcx (context, buffers, kernel launchers).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -86,6 +87,23 @@ struct PairTables {
     int max_rows = 0;          // rows of the largest block
 };
 
+// One uneven instance of a batched solve (device copy, read by the batch kernels).
+struct BatchInst {
+    int slot;                  // distinct-q slot (pair densities on the union G list of that q)
+    int ng;                    // N_G: the first ng entries of the slot's list
+    int head;                  // position of G = 0 in the list
+    int iq;                    // q index into the context's states
+    long long eps_off;         // double2 offset of eps [ng][ng] in the batch eps buffer
+    long long work_off;        // element offset of the LU work matrix [ng][ng+1]
+    const double* vs;          // [>= ng] v^1/2(q+G) of the slot's list
+    const double2* rho64;      // FP64 path: [U][nt] pair densities of the slot
+    double w;                  // frequency (Hartree)
+    long long vec_off;         // offset of the instance's vectors (pivot order, solution, residual)
+};
+#define QCX_BATCH_MAXQ 16      // distinct q per persistent tensor-core launch
+struct BatchPlan;
+void qcx_batch_destroy(BatchPlan* p);
+
 struct qcx_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -122,6 +140,10 @@ struct qcx_ctx {
     DevBuf scratch;            // host<->device staging for outputs
     DevBuf scratch2;
 
+    unsigned long long gen = 0;    // bumped whenever basis or states change
+    BatchPlan* batch = nullptr;    // cached plan (and captured graph) of the last batched solve
+    int batch_tune = 1;            // autotune the batch tiling when a new plan is built
+
     ~qcx_ctx();
     qcx_status fail(qcx_status s, const std::string& msg) {
         err = msg;
@@ -146,6 +168,35 @@ cudaError_t qcx_pair_density_configure();
 // chi0 (chi0_fp64.cu, chi0_tc.cu)
 cudaError_t qcx_launch_chi0_fp64(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out);
 cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out, int* d_status);
+// 2-D tensor map over one BF16 plane [rows][kp], box {32, box_rows}, 64-byte swizzle
+bool qcx_make_bf16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows);
+
+// persistent tensor-core chi0 over a tile list of uneven instances (chi0_tc_batch.cu).
+// maps: [nslot][3] tensor maps (box {32, 64}) of the BF16 planes of slots slot0 .. slot0 + nslot - 1;
+// tiles: {inst, gb, n0, N | src<<16}, every tile's instance in that slot range.
+cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, int slot0, int nslot, int ntile,
+                                     const int4* d_tiles, int grid, const BatchInst* d_inst, const float2* wtab,
+                                     long long wld, int kstages, double pref, double* acc64, double2* eps,
+                                     int* status);
+size_t qcx_chi0_tc_batch_acc_bytes(int grid);
+
+// batched solve for the heads of eps^-1 (batch_solve.cu)
+struct BatchSolveArgs {
+    const BatchInst* inst;
+    const int* cta_off;        // [grid + 1] instance lists per CTA (CSR)
+    const int* cta_ids;
+    const double2* eps;        // FP64 eps of every instance
+    void* work;                // LU factors ([ng][ng+1] per instance, FP32 or FP64 complex)
+    int* rowmap;               // [sum ng] pivot order: logical row -> stored row
+    double2* x;                // [sum ng] solution of A' x = e_last (refined in place)
+    double2* r;                // [sum ng] FP64 residual
+    double* out;               // [3][ninst]: L_LFE head, L_noLFE head, last relative correction
+    int* flags;                // [ninst]: 0 ok, 1 zero pivot, 2 refinement not converged
+    int ninst;
+};
+cudaError_t qcx_launch_lu_head(cudaStream_t st, const BatchSolveArgs& a, int grid, int nmax, bool fp64, bool want_x);
+cudaError_t qcx_launch_resid(cudaStream_t st, const BatchSolveArgs& a, const int2* tasks, int ntask);
+cudaError_t qcx_launch_lu_correct(cudaStream_t st, const BatchSolveArgs& a, int grid, int nmax, int last);
 
 // inverse + loss (invert.cu)
 cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double* d_loss_out);

@@ -52,6 +52,9 @@ _SIGS = {
     "qcx_loss_function": (I, [P, I, P, P]),
     "qcx_bin_loss": (I, [P, I, P, I, I, P, P, P]),
     "qcx_rate": (I, [P, I, P, I, P, P, ct.POINTER(HaloParams), P, I, P]),
+    "qcx_solve_batch": (I, [P, I, P, P, P, D, I, P, P, P]),
+    "qcx_batch_info": (I, [P, I, P]),
+    "qcx_batch_autotune": (I, [P, I]),
     "qcx_eps_inverse_diag_noalloc": (I, [P, I, I, P, P, P, P, P]),
 }
 
@@ -229,6 +232,32 @@ class Context:
         self._check(qcx_rate(self.h, len(qbin), qa.ptr, len(w), wa.ptr, La.ptr, ct.byref(params),
                              P(dR.ctypes.data), nQ, P(dQ.ctypes.data) if nQ else None))
         return dR, dQ[:nQ]
+
+    # ------------------------------------------------- batched instances
+    def solve_batch(self, inst_q, inst_w, inst_gmax, eta, prec=QCX_MIXED, out_lfe=None, out_nolfe=None,
+                    want_ng=True):
+        """Heads (L_LFE, L_noLFE) of uneven (q, w, G_max) instances; returns
+        (L_lfe[n], L_nolfe[n], N_G[n] or None).  Outputs may be device tensors."""
+        n = len(inst_q)
+        qa = _Arg(np.asarray(inst_q, np.int32) if not hasattr(inst_q, "data_ptr") else inst_q, np.int32)
+        wa, ga = _Arg(inst_w, np.float64), _Arg(inst_gmax, np.float64)
+        a = _out((n,), np.float64, out_lfe)
+        b = _out((n,), np.float64, out_nolfe)
+        ng = np.zeros(n, np.int32) if want_ng else None
+        aa, bb, na = _Arg(a, np.float64), _Arg(b, np.float64), _Arg(ng, np.int32)
+        self._check(qcx_solve_batch(self.h, n, qa.ptr, wa.ptr, ga.ptr, float(eta), prec, aa.ptr, bb.ptr, na.ptr))
+        return a, b, ng
+
+    def batch_info(self):
+        """Facts about the current batch plan (see qcx_batch_info)."""
+        out = (ct.c_longlong * 10)()
+        self._check(qcx_batch_info(self.h, 10, out))
+        keys = ["tile_cap", "tiles", "tc_ctas", "solve_ctas", "kernels_per_replay", "autotuned", "distinct_q",
+                "max_ng", "autotune_us", "precision"]
+        return dict(zip(keys, list(out)))
+
+    def batch_autotune(self, enable: bool):
+        self._check(qcx_batch_autotune(self.h, 1 if enable else 0))
 
     def sync(self):
         self._check(qcx_sync(self.h))
