@@ -19,6 +19,8 @@ Each function follows one step of the method as the paper states it:
   function Im[-1/eps] of Eq. (dynamic_structure_factor).
 * ``rate``: Eqs. (general_rate), (cross_section), (F_DM_limits),
   (excitation_rate) in the nonrelativistic halo limit of Appendix A.
+* ``mlp``: the learned local-field correction (no counterpart in the paper):
+  network, Gaussian negative log-likelihood, back-propagation and Adam.
 
 Parity status of every function is listed in the module docstrings; each is
 pinned by a test in ``tests/test_oracle_*.py``.

@@ -325,3 +325,14 @@ def make_tiny(seed: int = 7, shells_per_atom: int = 2, n_k: int = 2, nv: int = 2
     p = Problem("tiny", cell, basis, kp, q, G, nv, nc, Zk, Ek, Ekq,
                 omega_grid(50.0, nw), 0.5 / HARTREE_EV, seed=seed)
     return truncate(p, None, None)
+
+
+def mlp_init(seed: int = 2024, layers=(6, 128, 128, 128, 2)) -> np.ndarray:
+    """Initial parameters of the surrogate network as one FP32 vector (per
+    layer W [out][in] then b [out]): W ~ N(0, 1/fan_in), b = 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, o in zip(layers[:-1], layers[1:]):
+        parts.append(rng.standard_normal(o * i) / np.sqrt(i))
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
