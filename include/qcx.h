@@ -254,6 +254,62 @@ qcx_status qcx_batch_info(const qcx_ctx* ctx, int n, long long* out);
  * or off (then the widest tiles are used).  Errors: QCX_ERR_ARG (ctx NULL). */
 qcx_status qcx_batch_autotune(qcx_ctx* ctx, int enable);
 
+/* ----------------------------------------- learned local-field correction */
+
+/* A surrogate that the paper does not have: a network
+ * 6 -> 128 -> 128 -> 128 -> 2 (SiLU hidden activations) that maps the inputs
+ *   x = (|q| / q_max, q / |q| (3 components), w / w_max, ln(L_noLFE) / 10)
+ * of one (q, w) head to (mu, s): mu estimates y = log(L_LFE / L_noLFE) and
+ * s = log sigma^2 its uncertainty, so that L_LFE ~ L_noLFE e^mu can stand in
+ * for the Dyson route where sigma is small, with the Dyson route (the heads
+ * of qcx_solve_batch or of qcx_invert_eps) as fallback and judge.
+ * Parameters: one FP32 vector of QCX_MLP_NPARAM = 34178 entries, per layer
+ * W [out][in] row-major then b [out] (layers 6->128, 128->128, 128->128,
+ * 128->2).  Compute copies of the weight matrices are BF16; biases,
+ * activations, accumulations and gradients FP32.  Training minimises the
+ * Gaussian negative log-likelihood (s + (y - mu)^2 e^-s) / 2 averaged over
+ * each step's samples with Adam (bias-corrected), FP32 moments. */
+#define QCX_MLP_NPARAM 34178
+
+typedef struct {
+    int epochs;              /* passes over the data                              */
+    int batch;               /* samples per Adam step (last step of a pass: rest) */
+    float lr, beta1, beta2, eps;
+    unsigned long long seed; /* shuffle of each pass (Fisher-Yates, SplitMix64)   */
+} qcx_mlp_opts;
+
+/* QCX_MLP_NPARAM (for bindings). */
+int qcx_mlp_nparam(void);
+
+/* Load the FP32 parameters (host or device, QCX_MLP_NPARAM floats), refresh
+ * the BF16 copies and reset the Adam moments and step count.
+ * Errors: QCX_ERR_ARG (NULL, non-finite entry), QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_mlp_set_params(qcx_ctx* ctx, const float* params);
+
+/* Copy out the FP32 parameters and (if out_compute != NULL) the values the
+ * kernels compute with (BF16 weights widened to FP32, FP32 biases); either
+ * pointer may be host or device, QCX_MLP_NPARAM floats each.
+ * Errors: QCX_ERR_STATE (no parameters), QCX_ERR_CUDA. */
+qcx_status qcx_mlp_get_params(qcx_ctx* ctx, float* out_params, float* out_compute);
+
+/* Gradient of the mean loss over n samples X[n][6], y[n] with respect to
+ * the parameters (written to out_grad[QCX_MLP_NPARAM]) and the mean loss
+ * (out_loss, host, may be NULL).  No update.  Errors: QCX_ERR_STATE,
+ * QCX_ERR_ARG, QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_mlp_grad(qcx_ctx* ctx, int n, const float* X, const float* y, float* out_grad, double* out_loss);
+
+/* Train on X[n][6], y[n] (host or device) for opts->epochs shuffled passes;
+ * the pass is captured once as a CUDA graph and replayed.  out_epoch_loss
+ * (host, may be NULL) receives the mean loss of each pass (computed during
+ * the pass).  Errors: QCX_ERR_STATE, QCX_ERR_ARG, QCX_ERR_ALLOC,
+ * QCX_ERR_CUDA, QCX_ERR_NOT_CONVERGED (the loss became non-finite). */
+qcx_status qcx_mlp_train(qcx_ctx* ctx, int n, const float* X, const float* y, const qcx_mlp_opts* opts,
+                         float* out_epoch_loss);
+
+/* (mu, s) for X[n][6]; outputs host or device.  Errors: QCX_ERR_STATE,
+ * QCX_ERR_ARG, QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_mlp_predict(qcx_ctx* ctx, int n, const float* X, float* out_mu, float* out_logvar);
+
 /* ------------------------------------------------------- no allocation */
 
 /* The paper has no counterpart to this entry point; it exists for callers

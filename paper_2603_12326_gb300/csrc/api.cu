@@ -83,6 +83,7 @@ template <typename T> cudaError_t fetch(qcx_ctx* ctx, std::vector<T>& out, const
 
 qcx_ctx::~qcx_ctx() {
     qcx_batch_destroy(batch);
+    qcx_mlp_destroy(mlp);
     for (auto* l : loss) delete l;
     if (own_stream && stream) cudaStreamDestroy(stream);
 }

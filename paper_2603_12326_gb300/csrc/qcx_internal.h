@@ -103,6 +103,8 @@ struct BatchInst {
 #define QCX_BATCH_MAXQ 16      // distinct q per persistent tensor-core launch
 struct BatchPlan;
 void qcx_batch_destroy(BatchPlan* p);
+struct MlpState;
+void qcx_mlp_destroy(MlpState* m);
 
 struct qcx_ctx {
     int device = 0;
@@ -143,6 +145,7 @@ struct qcx_ctx {
     unsigned long long gen = 0;    // bumped whenever basis or states change
     BatchPlan* batch = nullptr;    // cached plan (and captured graph) of the last batched solve
     int batch_tune = 1;            // autotune the batch tiling when a new plan is built
+    MlpState* mlp = nullptr;       // surrogate network (parameters, Adam moments, work buffers)
 
     ~qcx_ctx();
     qcx_status fail(qcx_status s, const std::string& msg) {

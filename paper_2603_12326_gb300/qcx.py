@@ -55,6 +55,12 @@ _SIGS = {
     "qcx_solve_batch": (I, [P, I, P, P, P, D, I, P, P, P]),
     "qcx_batch_info": (I, [P, I, P]),
     "qcx_batch_autotune": (I, [P, I]),
+    "qcx_mlp_nparam": (I, []),
+    "qcx_mlp_set_params": (I, [P, P]),
+    "qcx_mlp_get_params": (I, [P, P, P]),
+    "qcx_mlp_grad": (I, [P, I, P, P, P, P]),
+    "qcx_mlp_train": (I, [P, I, P, P, P, P]),
+    "qcx_mlp_predict": (I, [P, I, P, P, P]),
     "qcx_eps_inverse_diag_noalloc": (I, [P, I, I, P, P, P, P, P]),
 }
 
@@ -89,6 +95,16 @@ def declared_symbols(header: str | None = None) -> list[str]:
     return sorted(set(re.findall(r"\b(qcx_[a-z0-9_]+)\s*\(", txt)))
 
 
+class MlpOpts(ct.Structure):
+    """qcx_mlp_opts."""
+    _fields_ = [("epochs", ct.c_int), ("batch", ct.c_int), ("lr", ct.c_float), ("beta1", ct.c_float),
+                ("beta2", ct.c_float), ("eps", ct.c_float), ("seed", ct.c_ulonglong)]
+
+
+def mlp_opts(epochs=100, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=1):
+    return MlpOpts(epochs, batch, lr, beta1, beta2, eps, seed)
+
+
 class QcxError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -104,7 +120,8 @@ class _Arg:
             self.ptr = None
         elif hasattr(x, "data_ptr"):
             import torch
-            want = {np.float64: torch.float64, np.complex128: torch.complex128, np.int32: torch.int32}[dtype]
+            want = {np.float64: torch.float64, np.complex128: torch.complex128, np.int32: torch.int32,
+                    np.float32: torch.float32}[dtype]
             if x.dtype != want or not x.is_contiguous():
                 raise TypeError(f"tensor must be contiguous {want}")
             self.ptr = P(x.data_ptr())
@@ -258,6 +275,41 @@ class Context:
 
     def batch_autotune(self, enable: bool):
         self._check(qcx_batch_autotune(self.h, 1 if enable else 0))
+
+    # ------------------------------------------- learned LFE correction
+    def mlp_set_params(self, params):
+        pa = _Arg(np.asarray(params, np.float32) if not hasattr(params, "data_ptr") else params, np.float32)
+        self._check(qcx_mlp_set_params(self.h, pa.ptr))
+
+    def mlp_get_params(self):
+        """(FP32 masters, values the kernels compute with)."""
+        n = qcx_mlp_nparam()
+        a = np.zeros(n, np.float32)
+        c = np.zeros(n, np.float32)
+        self._check(qcx_mlp_get_params(self.h, P(a.ctypes.data), P(c.ctypes.data)))
+        return a, c
+
+    def mlp_grad(self, X, y):
+        Xa, ya = _Arg(X, np.float32), _Arg(y, np.float32)
+        g = np.zeros(qcx_mlp_nparam(), np.float32)
+        loss = ct.c_double()
+        self._check(qcx_mlp_grad(self.h, len(y), Xa.ptr, ya.ptr, P(g.ctypes.data), ct.byref(loss)))
+        return loss.value, g
+
+    def mlp_train(self, X, y, opts: MlpOpts):
+        Xa, ya = _Arg(X, np.float32), _Arg(y, np.float32)
+        curve = np.zeros(opts.epochs, np.float32)
+        self._check(qcx_mlp_train(self.h, len(y), Xa.ptr, ya.ptr, ct.byref(opts), P(curve.ctypes.data)))
+        return curve
+
+    def mlp_predict(self, X, out_mu=None, out_logvar=None):
+        n = len(X)
+        Xa = _Arg(X, np.float32)
+        mu = _out((n,), np.float32, out_mu)
+        lv = _out((n,), np.float32, out_logvar)
+        ma, la = _Arg(mu, np.float32), _Arg(lv, np.float32)
+        self._check(qcx_mlp_predict(self.h, n, Xa.ptr, ma.ptr, la.ptr))
+        return mu, lv
 
     def sync(self):
         self._check(qcx_sync(self.h))
