@@ -310,6 +310,50 @@ qcx_status qcx_mlp_train(qcx_ctx* ctx, int n, const float* X, const float* y, co
  * QCX_ERR_ARG, QCX_ERR_ALLOC, QCX_ERR_CUDA. */
 qcx_status qcx_mlp_predict(qcx_ctx* ctx, int n, const float* X, float* out_mu, float* out_logvar);
 
+/* The surrogate route for the heads.  qcx_head_nolfe: L_noLFE at the head
+ * of q number iq for nw frequencies (Hartree, host or device), from
+ * eps_00 = 1 - v(q) chi0_00 with chi0_00 = 2/(N_k V) sum_t W_t |rho_t(q)|^2
+ * in FP64 (only rho at G = 0 is formed).  It uses the context's FP64 per-q
+ * state, so a later qcx_chi0 needs qcx_pair_density again.
+ * Errors: QCX_ERR_STATE, QCX_ERR_ARG (q = 0 among them), QCX_ERR_ALLOC,
+ * QCX_ERR_CUDA. */
+qcx_status qcx_head_nolfe(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, double* out_L_nolfe_head);
+
+/* Network inputs X[n][6] (FP32) from q vectors qvec[n][3] (bohr^-1),
+ * frequencies w[n] (Hartree) and L_noLFE[n]: (|q|/q_max, q/|q|, w/w_max,
+ * ln(L_noLFE)/10); with L_lfe[n] also the training targets
+ * out_y[n] = log(L_LFE / L_noLFE) (L_lfe and out_y both NULL or both set).
+ * Inputs and outputs host or device.  Errors: QCX_ERR_ARG, QCX_ERR_ALLOC,
+ * QCX_ERR_CUDA. */
+qcx_status qcx_surrogate_features(qcx_ctx* ctx, int n, const double* qvec, const double* w, const double* L_nolfe,
+                                  const double* L_lfe, double q_max, double w_max, float* out_X, float* out_y);
+
+typedef struct {
+    double q_max, w_max;       /* feature scaling (bohr^-1, Hartree), as in training          */
+    double sigma_accept;       /* accept where e^(s/2) < sigma_accept                        */
+    double check_frac;         /* fraction of accepted samples re-solved by the Dyson route  */
+    double check_tol;          /* spot check passes if |mu - log(L_LFE/L_noLFE)| <= check_tol */
+    unsigned long long seed;   /* choice of the spot-checked samples                          */
+} qcx_surrogate_opts;
+
+/* Heads for nsel q points (indices iq_list) x nw frequencies w (host), the
+ * Dyson route on the G list G_int[ng][3] (host; must contain G = 0) being the
+ * fallback: per sample the network predicts (mu, s) from qcx_head_nolfe's
+ * L_noLFE; L_LFE = L_noLFE e^mu is kept where e^(s/2) < sigma_accept; a
+ * seeded fraction check_frac of the kept samples is re-solved by the Dyson
+ * route (fallback_prec) and if any misses by more than check_tol in
+ * |log ratio| all samples fall back; rejected samples always take the Dyson
+ * route.  Outputs [nsel][nw] (host or device; L_nolfe and source may be
+ * NULL): out_L_lfe_head, out_L_nolfe_head, out_source (0 surrogate,
+ * 1 Dyson route, 2 Dyson route as a spot check), out_check_err (host: the
+ * largest spot-check miss, -1 if none was checked).  Replaces the context's
+ * per-q state.  Errors: QCX_ERR_STATE (no states or no network parameters),
+ * QCX_ERR_ARG, QCX_ERR_SINGULAR, QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_surrogate_heads(qcx_ctx* ctx, int nsel, const int* iq_list, int ng, const int* G_int, int nw,
+                               const double* w, double eta, qcx_precision fallback_prec,
+                               const qcx_surrogate_opts* opts, double* out_L_lfe_head, double* out_L_nolfe_head,
+                               int* out_source, double* out_check_err);
+
 /* ------------------------------------------------------- no allocation */
 
 /* The paper has no counterpart to this entry point; it exists for callers

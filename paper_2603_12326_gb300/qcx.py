@@ -61,6 +61,9 @@ _SIGS = {
     "qcx_mlp_grad": (I, [P, I, P, P, P, P]),
     "qcx_mlp_train": (I, [P, I, P, P, P, P]),
     "qcx_mlp_predict": (I, [P, I, P, P, P]),
+    "qcx_head_nolfe": (I, [P, I, I, P, D, P]),
+    "qcx_surrogate_features": (I, [P, I, P, P, P, P, D, D, P, P]),
+    "qcx_surrogate_heads": (I, [P, I, P, I, P, I, P, D, I, P, P, P, P, P]),
     "qcx_eps_inverse_diag_noalloc": (I, [P, I, I, P, P, P, P, P]),
 }
 
@@ -103,6 +106,12 @@ class MlpOpts(ct.Structure):
 
 def mlp_opts(epochs=100, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=1):
     return MlpOpts(epochs, batch, lr, beta1, beta2, eps, seed)
+
+
+class SurrogateOpts(ct.Structure):
+    """qcx_surrogate_opts."""
+    _fields_ = [("q_max", ct.c_double), ("w_max", ct.c_double), ("sigma_accept", ct.c_double),
+                ("check_frac", ct.c_double), ("check_tol", ct.c_double), ("seed", ct.c_ulonglong)]
 
 
 class QcxError(RuntimeError):
@@ -310,6 +319,38 @@ class Context:
         ma, la = _Arg(mu, np.float32), _Arg(lv, np.float32)
         self._check(qcx_mlp_predict(self.h, n, Xa.ptr, ma.ptr, la.ptr))
         return mu, lv
+
+    def head_nolfe(self, iq, w, eta):
+        wa = _Arg(w, np.float64)
+        out = np.zeros(len(w), np.float64)
+        self._check(qcx_head_nolfe(self.h, iq, len(w), wa.ptr, float(eta), P(out.ctypes.data)))
+        return out
+
+    def surrogate_features(self, qvec, w, L_nolfe, q_max, w_max, L_lfe=None):
+        """Network inputs X [n][6] and, with L_lfe, the targets y [n] (else None)."""
+        n = len(w)
+        qa, wa, La = _Arg(qvec, np.float64), _Arg(w, np.float64), _Arg(L_nolfe, np.float64)
+        L1 = _Arg(L_lfe, np.float64)
+        X = np.zeros((n, 6), np.float32)
+        y = np.zeros(n, np.float32) if L_lfe is not None else None
+        self._check(qcx_surrogate_features(self.h, n, qa.ptr, wa.ptr, La.ptr, L1.ptr, float(q_max), float(w_max),
+                                           P(X.ctypes.data), P(y.ctypes.data) if y is not None else None))
+        return X, y
+
+    def surrogate_heads(self, iq_list, G_int, w, eta, opts: SurrogateOpts, fallback_prec=QCX_MIXED):
+        """(L_lfe [nsel][nw], L_nolfe, source, largest spot-check miss)."""
+        iq = np.ascontiguousarray(iq_list, np.int32)
+        G = np.ascontiguousarray(G_int, np.int32)
+        wa = np.ascontiguousarray(w, np.float64)
+        nsel, nw = len(iq), len(wa)
+        L1 = np.zeros((nsel, nw), np.float64)
+        L2 = np.zeros((nsel, nw), np.float64)
+        src = np.zeros((nsel, nw), np.int32)
+        chk = ct.c_double()
+        self._check(qcx_surrogate_heads(self.h, nsel, P(iq.ctypes.data), len(G), P(G.ctypes.data), nw,
+                                        P(wa.ctypes.data), float(eta), fallback_prec, ct.byref(opts),
+                                        P(L1.ctypes.data), P(L2.ctypes.data), P(src.ctypes.data), ct.byref(chk)))
+        return L1, L2, src, chk.value
 
     def sync(self):
         self._check(qcx_sync(self.h))

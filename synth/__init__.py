@@ -254,6 +254,19 @@ def make_mid_shard(shard: int) -> Problem:
     return p
 
 
+def make_surrogate_set(nq: int = 110) -> Problem:
+    """The learned-correction workload: the mid workload's cell, basis, k grid
+    and bands with its own `nq` random q (|q| <= 4 reciprocal units) and k+q
+    states; 200 w each (nq x 200 head samples)."""
+    p = make_mid()
+    rng = np.random.default_rng([1236, 11])
+    p.name = "surrogate"
+    p.qpts = random_q(rng, p.cell, nq, 4.0, p.G_int)
+    p.Ekq = band_energies(rng, (nq, p.nk, p.nc), 1.1, 30.0)
+    p.q_index = np.arange(nq) + 5000
+    return p
+
+
 def make_large(nq: int | None = None, nw: int | None = None) -> Problem:
     """Large all-electron-style workload (seed 1239).  The raw draws at k+q
     are [nq][1728][144][144] complex; ask for a few q only."""
