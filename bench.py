@@ -305,6 +305,7 @@ def run_ours(args, ws, rank, local):
 
     # ------------------------------------------- batched uneven instances (rank 0, N=1)
     batched = batched_leg(stream) if (rank == 0 and ws == 1) else None
+    surro = surrogate_leg(stream) if (rank == 0 and ws == 1 and not args.no_surrogate) else None
 
     # -------------------------------------------------------- CPU oracle (rank 0, N=1)
     cpu = None
@@ -341,6 +342,8 @@ def run_ours(args, ws, rank, local):
             out["cpu_baseline"] = cpu
         if batched:
             out["batched"] = batched
+        if surro:
+            out["surrogate"] = surro
         print(json.dumps(out), flush=True)
     ctx.close()
 
@@ -388,6 +391,103 @@ def batched_leg(stream, reps=10):
             "plan": info, "gpu_launches_per_batch": info["kernels_per_replay"]}
 
 
+def surrogate_leg(stream):
+    """The learned correction on its own workload (110 q of the mid workload,
+    200 w each): heads by the mixed Dyson route, training on 100 q, judged on
+    the 10 others; then the surrogate route (accept where sigma < 1e-2, 5 %
+    spot check, Dyson fallback) on the held-out q."""
+    import torch
+
+    import synth
+    from paper_2603_12326_gb300 import QCX_MIXED, qcx, states, surrogate
+
+    ctx = qcx.Context(torch.cuda.current_device(), stream=stream.cuda_stream)
+    p = synth.make_surrogate_set()
+    L1, L2 = surrogate.head_table(ctx, p, range(p.nq))
+    unit = 2.0 * np.pi / p.cell.a
+    qmax, wmax = 4.0 * unit, float(p.w[-1])
+    ntr = 100
+    X, y, _ = surrogate.dataset(ctx, p, range(ntr), L1[:ntr], L2[:ntr], qmax, wmax)
+    Xt, yt, _ = surrogate.dataset(ctx, p, range(ntr, p.nq), L1[ntr:], L2[ntr:], qmax, wmax)
+    ctx.mlp_set_params(synth.mlp_init(2024))
+    epochs = 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    curve = ctx.mlp_train(X, y, qcx.mlp_opts(epochs=epochs, batch=256, lr=1e-3, seed=5))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    mu, lv = ctx.mlp_predict(Xt)
+    Xbig = np.tile(Xt, (max(1, 1000000 // len(Xt)), 1))
+    ctx.mlp_predict(Xbig)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.mlp_predict(Xbig)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pred_ms = e0.elapsed_time(e1)
+    te = list(range(ntr, p.nq))
+    states.load_problem(ctx, p, te)
+    opts = qcx.SurrogateOpts(qmax, wmax, 1e-2, 0.05, 1e-2, 7)
+    w = p.w[1:]
+    ctx.surrogate_heads(range(len(te)), p.G_int, w, p.eta, opts, QCX_MIXED)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, _, src, chk = ctx.surrogate_heads(range(len(te)), p.G_int, w, p.eta, opts, QCX_MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    route_ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"workload": "110 q of the mid workload x 200 w (heads), 100 q train / 10 q held out",
+            "train": {"samples": int(len(y)), "epochs": epochs, "ms": train_ms,
+                      "samples_per_s": len(y) * epochs / (train_ms / 1e3), "loss_first_last": [float(curve[0]),
+                                                                                               float(curve[-1])]},
+            "predict_samples_per_s": len(Xbig) / (pred_ms / 1e3),
+            "held_out": {"samples": int(len(yt)), "mae_log_ratio_network": float(np.mean(np.abs(mu - yt))),
+                         "mae_log_ratio_no_lfe": float(np.mean(np.abs(yt)))},
+            "route": {"value": len(te) * len(w) / (route_ms / 1e3), "unit": "blocks/s",
+                      "accepted_fraction": float(np.mean(src == 0)), "spot_checked": int(np.sum(src == 2)),
+                      "largest_spot_check_miss": chk,
+                      "note": "accept where sigma < 1e-2; the rest falls back to the mixed Dyson route"}}
+
+
+def run_profile_case_batch():
+    """The uneven workload once through qcx_solve_batch (mixed, no autotuning:
+    one capture, one replay) - every batch kernel launches once or twice."""
+    import torch
+
+    import synth
+    from paper_2603_12326_gb300 import QCX_MIXED, qcx, states
+    from paper_2603_12326_gb300.build import build
+    build()
+    ctx = qcx.Context(0)
+    p = synth.make_uneven()
+    states.load_problem(ctx, p)
+    ctx.batch_autotune(False)
+    e = p.extra
+    ctx.solve_batch(e["inst_q"], e["inst_w"], e["inst_gmax"], p.eta, QCX_MIXED)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("profile case done")
+
+
+def run_profile_case_mlp():
+    """One training step's gradient on 256 samples and a 20000-sample prediction."""
+    import synth
+    from paper_2603_12326_gb300 import qcx
+    from paper_2603_12326_gb300.build import build
+    build()
+    ctx = qcx.Context(0)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((20000, 6)).astype(np.float32)
+    y = rng.standard_normal(20000).astype(np.float32)
+    ctx.mlp_set_params(synth.mlp_init(1))
+    ctx.mlp_grad(X[:256], y[:256])
+    ctx.mlp_predict(X)
+    ctx.close()
+    print("profile case done")
+
+
 def run_profile_case():
     """1 q x 50 w of the mid workload through the mixed path, twice."""
     import torch
@@ -416,8 +516,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="small case for profilers: 1 q x 50 w of the mid workload, 2 passes, no report")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-correction leg")
+    ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "batch", "mlp"],
+                    help="small case for profilers, no report: mid = 1 q x 50 w of the mid workload, 2 passes; "
+                         "batch = the uneven workload once; mlp = one gradient and one prediction")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if ws > 1:
@@ -427,8 +529,12 @@ def main():
         if torch.cuda.is_available():
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
-    if args.profile_case:
+    if args.profile_case == "mid":
         run_profile_case()
+    elif args.profile_case == "batch":
+        run_profile_case_batch()
+    elif args.profile_case == "mlp":
+        run_profile_case_mlp()
     elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
