@@ -15,6 +15,8 @@
 #include "qcx_internal.h"
 #include "cplx.cuh"
 
+#include <cooperative_groups.h>
+
 namespace {
 
 constexpr int INV_THREADS = 512;
@@ -210,6 +212,225 @@ __global__ void __launch_bounds__(INV_THREADS) k_gauss_jordan(InvArgs<T> a, int 
     }
 }
 
+// Mixed path, N_G <= GJC_MAXN: the same elimination with the matrix resident
+// in shared memory, split by columns over a cluster of GJC_CS CTAs (a 181 x 181
+// FP32 complex matrix is 262 KB, more than one CTA holds).  Step k: the CTA
+// owning column k picks the pivot row and publishes the row index, the pivot
+// and column k after the row exchange (the multipliers) in its shared memory;
+// after one cluster barrier the others read them through distributed shared
+// memory; every CTA then exchanges rows, scales the pivot row and eliminates
+// in its own columns.  The published values alternate between two slots, so
+// the barrier of the next step also orders their reuse.  Warps take rows,
+// lanes take columns.
+constexpr int GJC_CS = 2;
+constexpr int GJC_THREADS = 512;
+constexpr int GJC_MAXN = 192;
+constexpr int GJC_WARPS = GJC_THREADS / 32;
+
+__global__ void __cluster_dims__(GJC_CS, 1, 1) __launch_bounds__(GJC_THREADS) k_gj_cluster(InvArgs<float> a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int b = blockIdx.x / GJC_CS;
+    const int n = a.ng;
+    const int h = (n + GJC_CS - 1) / GJC_CS;
+    const int c0 = rank * h;
+    const int hn = max(0, min(h, n - c0));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* Xs = reinterpret_cast<float2*>(smem_raw);     // [n][h] my columns
+    float2* F = Xs + (size_t)n * h;                        // [2][n] published multipliers
+    float2* Fl = F + 2 * n;                                // [n] multipliers of this step
+    float2* rowk = Fl + n;                                 // [h] scaled pivot row
+    int* piv = reinterpret_cast<int*>(rowk + h);           // [n]
+    int* idx = piv + n;                                    // [n]
+    int* jof = idx + n;                                    // [n] inverse of idx
+    __shared__ int s_p[2], s_bad[2];
+    __shared__ float2 s_pv[2];
+    __shared__ float red_v[GJC_WARPS];
+    __shared__ int red_i[GJC_WARPS];
+    __shared__ double s_anorm, s_xnorm;
+
+    const double2* A = a.eps64 + (size_t)b * n * n;
+    for (int i = warp; i < n; i += GJC_WARPS)
+        for (int c = lane; c < hn; c += 32) {
+            const double2 z = A[(size_t)i * n + c0 + c];
+            Xs[i * h + c] = make_float2((float)z.x, (float)z.y);
+            if (i == c0 + c) {
+                a.eps_diag[(size_t)b * n + i] = z;
+                a.L[((size_t)a.nw + b) * n + i] = z.y / (z.x * z.x + z.y * z.y);
+            }
+        }
+    if (threadIdx.x == 0) {
+        s_anorm = 0.0;
+        s_xnorm = 0.0;
+    }
+    __syncthreads();
+    if (a.kappa) {
+        double best = 0.0;
+        for (int c = threadIdx.x; c < hn; c += blockDim.x) {
+            double cs = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double2 z = A[(size_t)i * n + c0 + c];
+                cs += sqrt(z.x * z.x + z.y * z.y);
+            }
+            best = fmax(best, cs);
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
+        if (lane == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(&s_anorm), (unsigned long long)__double_as_longlong(best));
+    }
+    __syncthreads();
+
+    int bad = 0;
+    for (int k = 0; k < n; ++k) {
+        const int owner = k / h, kc = k - owner * h, par = k & 1;
+        if (rank == owner) {
+            float best = -1.0f;
+            int bi = n;
+            for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+                const float2 z = Xs[i * h + kc];
+                const float v = z.x * z.x + z.y * z.y;
+                if (v > best) {
+                    best = v;
+                    bi = i;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) {
+                    best = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                red_v[warp] = best;
+                red_i[warp] = bi;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float bv = red_v[0];
+                int bix = red_i[0];
+                for (int w = 1; w < GJC_WARPS; ++w)
+                    if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bix)) {
+                        bv = red_v[w];
+                        bix = red_i[w];
+                    }
+                const int sing = !(bv > 0.0f) || bix >= n;
+                if (sing) bix = k;
+                s_bad[par] = sing;
+                s_p[par] = bix;
+                s_pv[par] = Xs[bix * h + kc];
+            }
+            __syncthreads();
+            const int p = s_p[par];
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int src = (i == k) ? p : (i == p ? k : i);
+                F[par * n + i] = Xs[src * h + kc];
+            }
+        }
+        cl.sync();
+        const int p = cl.map_shared_rank(s_p, owner)[par];
+        bad = cl.map_shared_rank(s_bad, owner)[par];
+        const float2 pv = cl.map_shared_rank(s_pv, owner)[par];
+        if (bad) break;
+        const float2* Fr = cl.map_shared_rank(F, owner) + par * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) Fl[i] = Fr[i];
+        if (threadIdx.x == 0) piv[k] = p;
+        if (p != k)
+            for (int c = threadIdx.x; c < hn; c += blockDim.x) {
+                const float2 t = Xs[k * h + c];
+                Xs[k * h + c] = Xs[p * h + c];
+                Xs[p * h + c] = t;
+            }
+        __syncthreads();
+        const float d = 1.0f / (pv.x * pv.x + pv.y * pv.y);
+        const float2 inv = make_float2(pv.x * d, -pv.y * d);
+        for (int c = threadIdx.x; c < hn; c += blockDim.x)
+            rowk[c] = (rank == owner && c == kc) ? inv : cmul(Xs[k * h + c], inv);
+        __syncthreads();
+        for (int i = warp; i < n; i += GJC_WARPS) {
+            const float2 f = Fl[i];
+            for (int c = lane; c < hn; c += 32) {
+                const float2 r = rowk[c];
+                if (i == k) {
+                    Xs[k * h + c] = r;
+                } else {
+                    float2 x = (rank == owner && c == kc) ? make_float2(0.f, 0.f) : Xs[i * h + c];
+                    x.x -= f.x * r.x - f.y * r.y;
+                    x.y -= f.x * r.y + f.y * r.x;
+                    Xs[i * h + c] = x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (rank == 0) {
+            if (threadIdx.x == 0) {
+                a.flags[b] = 1;
+                if (a.kappa) a.kappa[b] = 0.0;
+            }
+            for (int j = threadIdx.x; j < n; j += blockDim.x) a.diag_inv[(size_t)b * n + j] = make_double2(0.0, 0.0);
+        }
+        cl.sync();    // no CTA leaves while another may still read its shared memory
+        return;
+    }
+    // the inverse's column j is the eliminated matrix's column idx[j]
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < n; ++c) idx[c] = c;
+        for (int kk = n - 1; kk >= 0; --kk) {
+            const int t = idx[kk];
+            idx[kk] = idx[piv[kk]];
+            idx[piv[kk]] = t;
+        }
+        if (rank == 0) a.flags[b] = 0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) jof[idx[j]] = j;
+    __syncthreads();
+    float2* Xg = a.X + (size_t)b * n * n;
+    for (int i = warp; i < n; i += GJC_WARPS)
+        for (int c = lane; c < hn; c += 32) Xg[(size_t)i * n + jof[c0 + c]] = Xs[i * h + c];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int cgl = idx[j] - c0;
+        if (cgl >= 0 && cgl < hn) {
+            const float2 z = Xs[j * h + cgl];
+            a.diag_inv[(size_t)b * n + j] = make_double2((double)z.x, (double)z.y);
+        }
+    }
+    if (a.kappa) {
+        double best = 0.0;
+        for (int c = threadIdx.x; c < hn; c += blockDim.x) {
+            double cs = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const float2 z = Xs[i * h + c];
+                cs += sqrt((double)z.x * z.x + (double)z.y * z.y);
+            }
+            best = fmax(best, cs);
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
+        if (lane == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(&s_xnorm), (unsigned long long)__double_as_longlong(best));
+    }
+    cl.sync();
+    if (a.kappa && rank == 0 && threadIdx.x == 0) {
+        double an = 0.0, xn = 0.0;
+        for (int r = 0; r < GJC_CS; ++r) {
+            an = fmax(an, *cl.map_shared_rank(&s_anorm, r));
+            xn = fmax(xn, *cl.map_shared_rank(&s_xnorm, r));
+        }
+        a.kappa[b] = an * xn;
+    }
+    cl.sync();    // rank 0 has read every CTA's norms
+}
+
+size_t gjc_smem(int n) {
+    const int h = (n + GJC_CS - 1) / GJC_CS;
+    return ((size_t)n * h + 3 * (size_t)n + h) * sizeof(float2) + 3 * (size_t)n * sizeof(int);
+}
+
 // FP64 correction of the diagonal of X ~ A^-1 for the ill-conditioned blocks
 // (A FP64, X FP32):  d_j = X_jj + sum_k X_jk (delta_kj - sum_l A_kl X_lj).
 // Grid (block, 32-column panel).  Well-conditioned blocks keep X_jj.
@@ -306,11 +527,19 @@ cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double
     a.eps_diag = s.eps_diag.as<double2>();
     a.L = d_loss_out;
     a.flags = s.flags.as<int>();
-    const size_t smem = (size_t)n * 2 * sizeof(float2) + (size_t)n * 2 * sizeof(int);
-    e = cudaFuncSetAttribute((const void*)k_gauss_jordan<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gauss_jordan<float><<<s.nw, INV_THREADS, smem, ctx->stream>>>(a, 0);
+    if (n <= GJC_MAXN) {
+        // the matrix stays in the shared memory of a 2-CTA cluster
+        const size_t smem = gjc_smem(n);
+        e = cudaFuncSetAttribute((const void*)k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gj_cluster<<<s.nw * GJC_CS, GJC_THREADS, smem, ctx->stream>>>(a);
+    } else {
+        const size_t smem = (size_t)n * 2 * sizeof(float2) + (size_t)n * 2 * sizeof(int);
+        e = cudaFuncSetAttribute((const void*)k_gauss_jordan<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gauss_jordan<float><<<s.nw, INV_THREADS, smem, ctx->stream>>>(a, 0);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.resid.p, 0, sizeof(double) * s.nw, ctx->stream);
