@@ -28,9 +28,10 @@
 // CTA work item: one 64-row G' block, one frequency (a 128 x N accumulator:
 // 64 re rows and 64 im rows), one N chunk of G.  Warp roles: warp 0 issues
 // TMA loads of the B tiles (and, when the G range is split, of the A-source
-// rows); warp 1 owns TMEM and issues the MMAs from one thread; warps 2-9 form
-// W and the A tiles, drain the accumulators and run the epilogue
-// (eps = delta - v^1/2 chi0 v^1/2).  Every wait is bounded: on timeout the
+// rows); warp 1 owns TMEM; one thread of warp 1 issues the MMAs of the even
+// accumulation windows and one thread of warp 10 those of the odd windows;
+// warps 2-9 form W and the A tiles, drain the accumulators and run the
+// epilogue (eps = delta - v^1/2 chi0 v^1/2); warp 11 idles.  Every wait is bounded: on timeout the
 // kernel records an error status, lets its own copies and MMAs finish, frees
 // TMEM and returns.
 #include "qcx_internal.h"
@@ -40,7 +41,8 @@
 
 namespace {
 
-constexpr int NTHREADS = 320;
+constexpr int NTHREADS = 384;                // warps: 0 TMA, 1 and 10 MMA, 2-9 A/drain/epilogue, 11 idle
+constexpr int MMA_WARP2 = 10;
 constexpr int NSTAGE = 3;
 constexpr int NPIECE = 3;                 // BF16 terms per operand
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&acc_full[b], 1);
             mbar_init(&drained[b], 8);
         }
-        mbar_init(mma_done, 1);
+        mbar_init(mma_done, 2);     // one commit per MMA issuer
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -139,44 +141,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (last >= 0)
                 mbar_wait(&full_b[last % NSTAGE], (uint32_t)(last / NSTAGE) & 1u, abort_flag, a.status, false);
         }
-    } else if (warp == 1) {
-        // ---------------------------------------------------------- MMA issuer
+    } else if (warp == 1 || warp == MMA_WARP2) {
+        // ---------------------------------------------------------- MMA issuers
+        // Issuing tcgen05.mma keeps the issuing thread busy for about as long as the
+        // MMAs run, so one thread's barrier waits and bookkeeping would leave the
+        // tensor pipe idle between stages.  Two issuers take alternate accumulation
+        // windows (TMEM buffer 0 and 1), so one waits while the other's MMAs run.
         if (lane == 0) {
+            const int par = warp == 1 ? 0 : 1;
             const uint32_t idesc = make_idesc(128, a.n_tile);
-            for (int it = 0; it < a.kstages; ++it) {
-                const int s = it % NSTAGE;
-                const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
-                const int win = it / PROMOTE, b = win & 1;
-                const bool first = (it % PROMOTE) == 0;
-                const bool last = (it % PROMOTE) == PROMOTE - 1 || it + 1 == a.kstages;
-                if (!mbar_wait(&full_b[s], ph, abort_flag, a.status)) break;
-                if (!mbar_wait(&full_a[s], ph, abort_flag, a.status)) break;
-                if (first && win >= 2 &&
-                    !mbar_wait(&drained[b], (uint32_t)((win - 2) >> 1) & 1u, abort_flag, a.status))
-                    break;
-                tc_fence_after();
-                unsigned char* st = base + s * stage_bytes;
-                const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes, b2 = b1 + bbytes;
-                const uint32_t d = tmem + (uint32_t)b * a.acc_off;
-                const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE, a2 = a1 + ATILE;
+            const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
+            bool ok = true;
+            for (int win = par; win < nwin && ok; win += 2) {
+                const int b = win & 1;
+                if (win >= 2 && !mbar_wait(&drained[b], (uint32_t)((win - 2) >> 1) & 1u, abort_flag, a.status)) break;
+                const int it1 = min((win + 1) * PROMOTE, a.kstages);
+                for (int it = win * PROMOTE; it < it1; ++it) {
+                    const int s = it % NSTAGE;
+                    const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+                    const bool first = it == win * PROMOTE;
+                    // the A warps arrive only after they saw this stage's copies land
+                    if (!mbar_wait(&full_a[s], ph, abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    unsigned char* st = base + s * stage_bytes;
+                    const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes, b2 = b1 + bbytes;
+                    const uint32_t d = tmem + (uint32_t)b * a.acc_off;
+                    const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE, a2 = a1 + ATILE;
 #pragma unroll
-                for (int kk = 0; kk < KSTEP / 16; ++kk) {
-                    const uint32_t off = kk * 32;
-                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
-                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
-                    umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                    umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
-                    umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
-                    umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                    for (int kk = 0; kk < KSTEP / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
+                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                    }
+                    umma_commit(&empty[s]);
                 }
-                umma_commit(&empty[s]);
-                if (last) umma_commit(&acc_full[b]);
+                if (ok) umma_commit(&acc_full[b]);
             }
-            // no MMA may still be running when TMEM is freed (also on the abort path)
+            // no MMA of either issuer may still be running when TMEM is freed (also on the abort path)
             umma_commit(mma_done);
             mbar_wait(mma_done, 0, abort_flag, a.status, false);
         }
-    } else {
+    } else if (warp < MMA_WARP2) {
         // --------------------------------- A generation, accumulator drain, epilogue
         const int wi = warp - 2;            // 0..7
         const int g = threadIdx.x - 64;     // 0..255
@@ -236,7 +248,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int it = 0; it < a.kstages && ok; ++it) {
             const int s = it % NSTAGE;
             const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
-            if (!(ok = warp_wait(&empty[s], ph ^ 1u, abort_flag, a.status))) break;
+            // the producer issued this stage's copies only after the MMAs of its previous use
+            // finished, so a landed stage is also free to overwrite
             if (!(ok = warp_wait(&full_b[s], ph, abort_flag, a.status))) break;
             unsigned char* st = base + s * stage_bytes;
             const unsigned char* srcb = a.src_from_b ? st : st + NPIECE * bbytes;
@@ -263,7 +276,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const float xr = wq.x * rr - wq.y * ri;
                     const float xi = wq.x * ri + wq.y * rr;
                     split3(xr, xi, re0[qq], re1[qq], re2[qq]);
-                    split3(xi, -xr, im0[qq], im1[qq], im2[qq]);
+                    // (xi, -xr) splits into the same terms as (xr, xi), swapped, the second negated
+                    im0[qq] = __byte_perm(re0[qq], 0u, 0x1032) ^ 0x80000000u;
+                    im1[qq] = __byte_perm(re1[qq], 0u, 0x1032) ^ 0x80000000u;
+                    im2[qq] = __byte_perm(re2[qq], 0u, 0x1032) ^ 0x80000000u;
                 }
             }
             unsigned char* ap = st + aoff;

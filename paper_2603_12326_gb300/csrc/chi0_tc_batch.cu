@@ -10,7 +10,8 @@
 // registers into an FP64 buffer, and eps = delta - v^1/2 chi0 v^1/2 written in
 // FP64 (row G', column G).
 //
-// What changes is the scheduling.  One CTA per SM runs for the whole batch
+// What changes is the scheduling (and, as in the per-q kernel, two MMA issuer
+// warps take alternate accumulation windows).  One CTA per SM runs for the whole batch
 // and walks a host-ordered tile list (largest N first, tile i to CTA
 // i mod grid), so hundreds of small instances cost one launch.  The shared
 // memory ring and the two TMEM accumulators keep their phases across tile
@@ -27,7 +28,8 @@
 
 namespace {
 
-constexpr int NTHREADS = 320;
+constexpr int NTHREADS = 384;             // warps: 0 TMA, 1 and 10 MMA, 2-9 A/drain/epilogue, 11 idle
+constexpr int MMA_WARP2 = 10;
 constexpr int NSTAGE = 3;
 constexpr int NPIECE = 3;
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
             mbar_init(&acc_full[b], 1);
             mbar_init(&drained[b], 8);
         }
-        mbar_init(mma_done, 1);
+        mbar_init(mma_done, 2);     // one commit per MMA issuer
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -140,54 +142,62 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
             if (last >= 0)
                 mbar_wait(&full_b[last % NSTAGE], (uint32_t)(last / NSTAGE) & 1u, abort_flag, a.status, false);
         }
-    } else if (warp == 1) {
-        // ---------------------------------------------------------- MMA issuer
+    } else if (warp == 1 || warp == MMA_WARP2) {
+        // ---------------------------------------------------------- MMA issuers
+        // Two issuers take alternate accumulation windows (counted over the CTA's whole
+        // tile sequence), so one waits while the other's MMAs run.
         if (lane == 0) {
-            int gs = 0, wbase = 0;
+            const int par = warp == 1 ? 0 : 1;
             bool ok = true;
-            for (int ti = blockIdx.x; ti < a.ntile && ok; ti += gridDim.x) {
-                const int4 tl = a.tiles[ti];
-                const int nN = tl.w & 0xFFFF;
-                const uint32_t idesc = make_idesc(128, nN);
-                for (int it = 0; it < a.kstages; ++it, ++gs) {
-                    const int s = (int)(gs % NSTAGE);
-                    const uint32_t ph = (uint32_t)(gs / NSTAGE) & 1u;
-                    const int gw = wbase + it / PROMOTE;
-                    const int b = (int)(gw & 1);
-                    const bool first = (it % PROMOTE) == 0;
-                    const bool lastw = (it % PROMOTE) == PROMOTE - 1 || it + 1 == a.kstages;
-                    if (!mbar_wait(&full_b[s], ph, abort_flag, a.status) ||
-                        !mbar_wait(&full_a[s], ph, abort_flag, a.status) ||
-                        (first && gw >= 2 &&
-                         !mbar_wait(&drained[b], (uint32_t)((gw - 2) >> 1) & 1u, abort_flag, a.status))) {
+            for (int lt = 0; blockIdx.x + lt * gridDim.x < a.ntile && ok; ++lt) {
+                const int4 tl = a.tiles[blockIdx.x + lt * gridDim.x];
+                const uint32_t idesc = make_idesc(128, tl.w & 0xFFFF);
+                for (int wd = 0; wd < nwin && ok; ++wd) {
+                    const int gw = lt * nwin + wd;
+                    if ((gw & 1) != par) continue;
+                    const int b = gw & 1;
+                    if (gw >= 2 && !mbar_wait(&drained[b], (uint32_t)((gw - 2) >> 1) & 1u, abort_flag, a.status)) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    unsigned char* st = base + s * STAGE_BYTES;
-                    const uint32_t b0 = smem_u32(st), b1 = b0 + BREG, b2 = b1 + BREG;
-                    const uint32_t d = tmem + (uint32_t)b * ACC_OFF;
-                    const uint32_t a0 = smem_u32(st + NPIECE * BREG + NPIECE * SPIECE), a1 = a0 + ATILE,
-                                   a2 = a1 + ATILE;
+                    const int it1 = min((wd + 1) * PROMOTE, a.kstages);
+                    for (int it = wd * PROMOTE; it < it1; ++it) {
+                        const int gs = lt * a.kstages + it;
+                        const int s = gs % NSTAGE;
+                        const uint32_t ph = (uint32_t)(gs / NSTAGE) & 1u;
+                        const bool first = it == wd * PROMOTE;
+                        // the A warps arrive only after they saw this stage's copies land
+                        if (!mbar_wait(&full_a[s], ph, abort_flag, a.status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        unsigned char* st = base + s * STAGE_BYTES;
+                        const uint32_t b0 = smem_u32(st), b1 = b0 + BREG, b2 = b1 + BREG;
+                        const uint32_t d = tmem + (uint32_t)b * ACC_OFF;
+                        const uint32_t a0 = smem_u32(st + NPIECE * BREG + NPIECE * SPIECE), a1 = a0 + ATILE,
+                                       a2 = a1 + ATILE;
 #pragma unroll
-                    for (int kk = 0; kk < KSTEP / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                        for (int kk = 0; kk < KSTEP / 16; ++kk) {
+                            const uint32_t off = kk * 32;
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc,
+                                      (first && kk == 0) ? 0u : 1u);
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                        }
+                        umma_commit(&empty[s]);
                     }
-                    umma_commit(&empty[s]);
-                    if (lastw) umma_commit(&acc_full[b]);
+                    if (ok) umma_commit(&acc_full[b]);
                 }
-                wbase += nwin;
             }
+            // no MMA of either issuer may still be running when TMEM is freed
             umma_commit(mma_done);
             mbar_wait(mma_done, 0, abort_flag, a.status, false);
         }
-    } else {
+    } else if (warp < MMA_WARP2) {
         // ------------------------- A generation, accumulator drain, epilogue
         const int wi = warp - 2;
         const int g = threadIdx.x - 64;
@@ -256,7 +266,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                 const int gs = lt * a.kstages + it;
                 const int s = gs % NSTAGE;
                 const uint32_t ph = (uint32_t)(gs / NSTAGE) & 1u;
-                if (!(ok = warp_wait(&empty[s], ph ^ 1u, abort_flag, a.status))) break;
+                // the producer issued this stage's copies only after the MMAs of its previous
+                // use finished, so a landed stage is also free to overwrite
                 if (!(ok = warp_wait(&full_b[s], ph, abort_flag, a.status))) break;
                 unsigned char* st = base + s * STAGE_BYTES;
                 const unsigned char* srcb = st + (src_b ? 0 : NPIECE * BREG);
@@ -282,7 +293,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                         const float xr = wq.x * rr - wq.y * ri;
                         const float xi = wq.x * ri + wq.y * rr;
                         split3(xr, xi, re0[qq], re1[qq], re2[qq]);
-                        split3(xi, -xr, im0[qq], im1[qq], im2[qq]);
+                        // (xi, -xr) splits into the terms of (xr, xi), swapped, the second negated
+                        im0[qq] = __byte_perm(re0[qq], 0u, 0x1032) ^ 0x80000000u;
+                        im1[qq] = __byte_perm(re1[qq], 0u, 0x1032) ^ 0x80000000u;
+                        im2[qq] = __byte_perm(re2[qq], 0u, 0x1032) ^ 0x80000000u;
                     }
                 }
                 unsigned char* ap = st + NPIECE * BREG + NPIECE * SPIECE;
