@@ -491,6 +491,88 @@ __global__ void __launch_bounds__(256) k_refine_diag(int n, const double2* Aall,
     }
 }
 
+// L_LFE of the mixed path without cancellation: for X = A^-1 (the FP32
+// inverse) and B = (A - A^H)/(2i) the Hermitian form of A's anti-Hermitian
+// part, -Im [A^-1]_jj = [X B X^H]_jj.  Where the loss is small against
+// |[A^-1]_jj| (Im of an O(1) diagonal) the imaginary part of the FP32 diagonal
+// loses its relative accuracy; the form builds L from the small B itself
+// (B from the FP64 matrix in FP64, rounded once), so its relative error is
+// that of X.  One CTA per (block, 32 rows j): T = X B in 32 x 32 tiles, then
+// L_j = Re sum_l T_jl conj(X_jl); the imaginary part of the reported diagonal
+// becomes -L_j.  Blocks corrected in FP64 keep their values.
+constexpr int QF = 32;
+__global__ void __launch_bounds__(256) k_loss_quadform(int n, const double2* Aall, const float2* Xall,
+                                                       const int* flags, const double* kappa, double2* diag_inv,
+                                                       double* L) {
+    __shared__ float2 Xs[QF][QF + 1];
+    __shared__ float2 Bs[QF][QF + 1];
+    __shared__ float Lrow[QF];
+    const int b = blockIdx.x, j0 = blockIdx.y * QF;
+    if (flags[b] || kappa[b] > KAPPA_REFINE) return;
+    const double2* A = Aall + (size_t)b * n * n;
+    const float2* X = Xall + (size_t)b * n * n;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (threadIdx.x < QF) Lrow[threadIdx.x] = 0.0f;
+    for (int l0 = 0; l0 < n; l0 += QF) {
+        float2 acc[2][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) acc[r][c] = make_float2(0.f, 0.f);
+        for (int k0 = 0; k0 < n; k0 += QF) {
+            for (int e = threadIdx.x; e < QF * QF; e += blockDim.x) {
+                const int r = e / QF, c = e % QF;
+                const int j = j0 + r, kk = k0 + c;
+                Xs[r][c] = (j < n && kk < n) ? X[(size_t)j * n + kk] : make_float2(0.f, 0.f);
+                const int kr = k0 + r, lc = l0 + c;
+                float2 bv = make_float2(0.f, 0.f);
+                if (kr < n && lc < n) {
+                    const double2 akl = A[(size_t)kr * n + lc], alk = A[(size_t)lc * n + kr];
+                    bv = make_float2((float)(0.5 * (akl.y + alk.y)), (float)(-0.5 * (akl.x - alk.x)));
+                }
+                Bs[r][c] = bv;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < QF; ++kk) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float2 x = Xs[ty + 16 * r][kk];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const float2 bb = Bs[kk][tx + 16 * c];
+                        acc[r][c].x = fmaf(x.x, bb.x, fmaf(-x.y, bb.y, acc[r][c].x));
+                        acc[r][c].y = fmaf(x.x, bb.y, fmaf(x.y, bb.x, acc[r][c].y));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // L_j += Re sum_l T_jl conj(X_jl) over this column tile
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int j = j0 + ty + 16 * r;
+            float part = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int l = l0 + tx + 16 * c;
+                if (j < n && l < n) {
+                    const float2 x = X[(size_t)j * n + l];
+                    part = fmaf(acc[r][c].x, x.x, fmaf(acc[r][c].y, x.y, part));
+                }
+            }
+            for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, 16);
+            if (tx == 0) Lrow[ty + 16 * r] += part;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < QF && j0 + threadIdx.x < n) {
+        const size_t o = (size_t)b * n + j0 + threadIdx.x;
+        L[o] = (double)Lrow[threadIdx.x];
+        diag_inv[o].y = -(double)Lrow[threadIdx.x];
+    }
+}
+
 }  // namespace
 
 cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double* d_loss_out) {
@@ -547,5 +629,9 @@ cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double
     dim3 grid(s.nw, (n + RF_COLS - 1) / RF_COLS);
     k_refine_diag<<<grid, 256, 0, ctx->stream>>>(n, a.eps64, a.X, a.flags, a.kappa, a.diag_inv, d_loss_out,
                                                   s.resid.as<double>());
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 gq(s.nw, (n + QF - 1) / QF);
+    k_loss_quadform<<<gq, 256, 0, ctx->stream>>>(n, a.eps64, a.X, a.flags, a.kappa, a.diag_inv, d_loss_out);
     return cudaGetLastError();
 }

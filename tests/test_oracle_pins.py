@@ -433,3 +433,24 @@ def test_g_shell_counts():
     for bound, n in ((4, 15), (8, 27), (32, 181), (48, 339), (59, 531)):
         assert int(np.sum(g2 / unit2 <= bound + 1e-9)) == n
     assert cell.volume == pytest.approx(cell.a ** 3 / 4)
+
+
+def test_loss_as_quadratic_form_of_the_anti_hermitian_part():
+    """-Im [A^-1]_jj = [A^-1 B A^-H]_jj with B = (A - A^H)/(2i) for any
+    invertible A (A^-1 - A^-H = A^-1 (A^H - A) A^-H).  The mixed GPU path
+    evaluates L_LFE this way, so that a small loss is formed from the small
+    anti-Hermitian part instead of the imaginary part of an O(1) number; here
+    the identity is checked on the oracle's dielectric matrices, plain and
+    transposed (the GPU stores eps^T), and a planted transpose of the inverse
+    in the quadratic form fails."""
+    p = synth.make_tiny(seed=3, shells_per_atom=2, n_k=2, nv=2, nc=3, ng=9, nq=1, nw=6)
+    Ck, Ckq = rpa.states(p, 0)
+    o = rpa.solve_q(p, 0, Ck, Ckq)
+    for A in (o["eps"], np.transpose(o["eps"], (0, 2, 1))):
+        X = np.linalg.inv(A)
+        B = (A - np.conj(np.transpose(A, (0, 2, 1)))) / 2j
+        quad = np.einsum("wjk,wkl,wjl->wj", X, B, np.conj(X))
+        assert np.max(np.abs(quad.imag)) < 1e-12 * np.max(np.abs(quad))
+        assert np.allclose(quad.real, o["L_lfe"], rtol=1e-10, atol=1e-14)
+        bad = np.einsum("wkj,wkl,wjl->wj", X, B, np.conj(X))
+        assert not np.allclose(bad.real, o["L_lfe"], rtol=1e-3)
