@@ -315,7 +315,9 @@ def run_ours(args, ws, rank, local):
                "seconds": round(secs, 2)}
 
     if rank == 0:
-        launches_per_step = nq * 6 + 2 + 4       # per q: setup, pair density, chi0, GJ, refine, |q+G|; bins; rate
+        # per q: G setup, pair densities, W table, chi0, Gauss-Jordan, FP64 diagonal correction, loss by the
+        # quadratic form, |q+G|; per step two binnings and two rate + recoil pairs
+        launches_per_step = nq * 8 + 2 + 4
         out = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "bf16",

@@ -51,6 +51,7 @@ constexpr int PROMOTE = 2;                // K stages accumulated in one TMEM bu
 constexpr int FLUSH = 128;                // stages between FP64 flushes of the register partials
 constexpr int MAXHALF = 96;               // columns of the accumulator one thread drains (n_tile/2)
 constexpr int SMEM_LIMIT = 232448;
+constexpr int PREFETCH = 4;               // K stages between the L2 prefetch of a stage and its copy
 
 struct TcArgs {
     int ng, nw, nv, nc;
@@ -117,10 +118,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
+            // a stage's lines are requested into L2 a few stages before its copy is issued
+            auto prefetch = [&](int it) {
+                bulk_prefetch(a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2));
+                tma_prefetch_2d(&mb0, it * KSTEP, n0);
+                tma_prefetch_2d(&mb1, it * KSTEP, n0);
+                tma_prefetch_2d(&mb2, it * KSTEP, n0);
+                if (!a.src_from_b) {
+                    tma_prefetch_2d(&ms0, it * KSTEP, gb * GBLK);
+                    tma_prefetch_2d(&ms1, it * KSTEP, gb * GBLK);
+                    tma_prefetch_2d(&ms2, it * KSTEP, gb * GBLK);
+                }
+            };
+            for (int it = 0; it < PREFETCH && it < a.kstages; ++it) prefetch(it);
             int last = -1;
             for (int it = 0; it < a.kstages; ++it) {
                 const int s = it % NSTAGE;
                 const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+                if (it + PREFETCH < a.kstages) prefetch(it + PREFETCH);
                 if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status)) break;
                 unsigned char* st = base + s * stage_bytes;
                 mbar_arrive_tx(&full_b[s], NPIECE * bbytes + sbytes + TPS * (uint32_t)sizeof(float2));

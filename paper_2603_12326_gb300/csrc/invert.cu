@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(256) k_loss_quadform(int n, const double2* Aal
                                                        double* L) {
     __shared__ float2 Xs[QF][QF + 1];
     __shared__ float2 Bs[QF][QF + 1];
+    __shared__ double2 At[QF][QF + 1];       // A_lk tile, read along rows, used transposed
     __shared__ float Lrow[QF];
     const int b = blockIdx.x, j0 = blockIdx.y * QF;
     if (flags[b] || kappa[b] > KAPPA_REFINE) return;
@@ -522,12 +523,17 @@ __global__ void __launch_bounds__(256) k_loss_quadform(int n, const double2* Aal
         for (int k0 = 0; k0 < n; k0 += QF) {
             for (int e = threadIdx.x; e < QF * QF; e += blockDim.x) {
                 const int r = e / QF, c = e % QF;
+                At[r][c] = (l0 + r < n && k0 + c < n) ? A[(size_t)(l0 + r) * n + k0 + c] : make_double2(0.0, 0.0);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < QF * QF; e += blockDim.x) {
+                const int r = e / QF, c = e % QF;
                 const int j = j0 + r, kk = k0 + c;
                 Xs[r][c] = (j < n && kk < n) ? X[(size_t)j * n + kk] : make_float2(0.f, 0.f);
                 const int kr = k0 + r, lc = l0 + c;
                 float2 bv = make_float2(0.f, 0.f);
                 if (kr < n && lc < n) {
-                    const double2 akl = A[(size_t)kr * n + lc], alk = A[(size_t)lc * n + kr];
+                    const double2 akl = A[(size_t)kr * n + lc], alk = At[c][r];
                     bv = make_float2((float)(0.5 * (akl.y + alk.y)), (float)(-0.5 * (akl.x - alk.x)));
                 }
                 Bs[r][c] = bv;
