@@ -1,0 +1,62 @@
+"""Parity at the largest workload (18 sp shells per atom with core exponents up
+to 5000 bohr^-2, 12^3 k, N_v = 14, N_c = 64, N_t = 1 548 288, N_G = 531, one q,
+all 400 w on 0-100 eV in one chi0 launch, eta = 0.05 eV) through the mixed
+path.  The oracle cannot form the whole 531 x 531 problem, so it computes the
+pair densities of four sampled G vectors (the head, its neighbour, a middle
+one and the largest |q+G|) over every transition and from them the sampled
+4 x 4 blocks of chi0 and the no-LFE loss of those G at four frequencies.  The
+whole loss tables are checked for what holds at any size: finite, and no
+negative loss above w = 0.  Tolerances as in the other mixed parity tests:
+chi0 5e-5 of the largest sampled element, L_noLFE 1e-4 relative (per G where
+L > 1e-3 of its maximum over the sampled frequencies)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import rpa
+from paper_2603_12326_gb300 import QCX_MIXED
+from tests.gpu_util import context, set_oracle_states
+
+pytestmark = pytest.mark.gpu
+SAMPLE_G = np.array([0, 1, 100, 530])
+SAMPLE_W = np.array([40, 120, 200, 300])
+
+
+@pytest.fixture(scope="module")
+def large():
+    p = synth.make_large(nq=1)
+    Ck, Ckq = rpa.states(p, 0)
+    c, b = p.cell, p.basis
+    Gc = p.G_int[SAMPLE_G] @ c.recip
+    kappa = p.qpts[0][None, :] + Gc
+    rho = rpa.pair_density_lean(c.lattice, c.atoms, b.shell_atom, b.shell_l, b.shell_exp, p.kpts, kappa, Ck, Ckq)
+    dE = rpa.transition_energies(p.Ek, p.Ekq[0])
+    W = rpa.transition_weights(dE, p.w[SAMPLE_W], p.eta)
+    chi = rpa.chi0(rho, W, p.nk, c.volume)
+    vs = rpa.coulomb_sqrt(p.qpts[0], Gc)
+    d = 1.0 - vs[None, :] ** 2 * np.einsum("wgg->wg", chi)
+    L_nolfe = (-(1.0 / d)).imag
+    return p, Ck, Ckq, chi, L_nolfe
+
+
+def test_large_workload_full_size_mixed(large):
+    p, Ck, Ckq, chi_o, L2_o = large
+    assert p.G_int.shape[0] == 531 and p.nk * p.nv * p.nc == 1548288 and p.w.shape[0] == 400
+    ctx = context()
+    set_oracle_states(ctx, p, [0], Ck, [Ckq])
+    ctx.pair_density(0, p.G_int, QCX_MIXED)
+    chi = ctx.chi0(0, p.w, p.eta, QCX_MIXED, want=True)         # all 400 w in one launch
+    ctx.invert_eps(0, QCX_MIXED, want=False)
+    L1, L2 = ctx.loss_function(0, QCX_MIXED)
+    ctx.close()
+    blk = chi[SAMPLE_W][:, SAMPLE_G][:, :, SAMPLE_G]
+    e_chi = float(np.max(np.abs(blk - chi_o)) / np.max(np.abs(chi_o)))
+    o = L2_o
+    top = np.max(np.abs(o), axis=0, keepdims=True)
+    m = np.abs(o) > 1e-3 * top
+    got = L2[SAMPLE_W][:, SAMPLE_G]
+    e2 = float(np.max(np.abs(got[m] - o[m]) / np.abs(o[m])))
+    print(f"large full size, mixed: sampled chi0 {e_chi:.2e}, sampled L_noLFE {e2:.2e}")
+    assert e_chi < 5e-5 and e2 < 1e-4
+    assert np.all(np.isfinite(L1)) and np.all(np.isfinite(L2))
+    assert np.all(L1[1:] > -1e-8) and np.all(L2[1:] > -1e-8)
