@@ -21,11 +21,13 @@
 #include "qcx_internal.h"
 #include "cplx.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace {
 
 constexpr int PD_THREADS = 256;
+constexpr int PDF_MAXT = 384;          // threads of the fused mixed-path kernel at most
 constexpr double LATTICE_CUT = 46.0;   // Gaussian prefactors below e^-46 ~ 1e-20 are dropped
 
 template <typename T> struct PDArgs {
@@ -71,10 +73,11 @@ template <typename C> __device__ __forceinline__ C cpow_int(C z, int n) {
     return r;
 }
 
-// One group pair's block of B into shared memory (row offset row0).
+// One group pair's 4 x 4 block of B (components s, p_x, p_y, p_z of each group;
+// absent components are left unset).
 template <typename T, int NCH>
-__device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T kk[3], const T kap[3], T k2,
-                                           cplx<T>* Bs, int row0) {
+__device__ __forceinline__ void pair_block_vals(const PDArgs<T>& a, int ip, const T kk[3], const T kap[3], T k2,
+                                                cplx<T> (&out)[4][4]) {
     using C = cplx<T>;
     const int ga = ip / a.ngrp, gb = ip % a.ngrp;
     const T* par = a.par + (size_t)ip * 8;
@@ -118,10 +121,8 @@ __device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T k
                                cscale(M0, inv2p - tk * tk));                  // E(1,1)
         }
     }
-    // components: 0 = s, 1..3 = p_x, p_y, p_z; present ones map to consecutive basis rows
+    // components: 0 = s, 1..3 = p_x, p_y, p_z
     const int ma = a.grp_mask[ga], mb = a.grp_mask[gb];
-    const int mu0 = a.grp_mu0[ga] - row0 - ((ma & 1) ? 0 : 1);
-    const int nu0 = a.grp_mu0[gb] - ((mb & 1) ? 0 : 1);
     const T fa = T(2) * sqrt(ap * p), fb = T(2) * sqrt(bp * p);   // p normalisation 2 sqrt(alpha)
 #pragma unroll
     for (int ca = 0; ca < 4; ++ca) {
@@ -139,10 +140,31 @@ __device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T k
                     val = cadd(val, prod);
                 }
                 const T f = (ca ? fa : T(1)) * (cb ? fb : T(1));
-                Bs[(mu0 + ca) * a.ldB + nu0 + cb] = cscale(cmul(common, val), f);
+                out[ca][cb] = cscale(cmul(common, val), f);
             }
         }
     }
+}
+
+// One group pair's block of B into shared memory (row offset row0); present
+// components map to consecutive basis rows and columns.
+template <typename T, int NCH>
+__device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T kk[3], const T kap[3], T k2,
+                                           cplx<T>* Bs, int row0) {
+    cplx<T> blk[4][4];
+    pair_block_vals<T, NCH>(a, ip, kk, kap, k2, blk);
+    const int ga = ip / a.ngrp, gb = ip % a.ngrp;
+    const int ma = a.grp_mask[ga], mb = a.grp_mask[gb];
+    const int mu0 = a.grp_mu0[ga] - row0 - ((ma & 1) ? 0 : 1);
+    const int nu0 = a.grp_mu0[gb] - ((mb & 1) ? 0 : 1);
+#pragma unroll
+    for (int ca = 0; ca < 4; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < 4; ++cb) {
+            const bool oka = ca == 0 ? (ma & 1) : (ma & 2);
+            const bool okb = cb == 0 ? (mb & 1) : (mb & 2);
+            if (oka && okb) Bs[(mu0 + ca) * a.ldB + nu0 + cb] = blk[ca][cb];
+        }
 }
 
 __device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
@@ -205,6 +227,90 @@ __global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
                 a.R2[o] = __halves2bfloat162(r2, i2);
             }
         }
+    }
+}
+
+// Mixed path, fused: one thread per (G, group a) walks every group b, forms the
+// 4 x 4 pair block in registers and adds it straight into its rows of
+// Y = B C_k (NV >= nv columns in registers), so B never goes through shared
+// memory.  Threads are ordered G fastest, so a warp holds one or two groups a
+// and every thread of it runs the same pair's lattice sums.  Y then goes to
+// shared memory and rho = C_kq^H Y is formed per (G, v, c).  The sums run in
+// the same order as in k_pair_density.
+template <int NV> constexpr int pdf_maxt() { return NV <= 4 ? PDF_MAXT : (NV <= 8 ? 256 : 192); }
+
+template <int NCH, int NV>
+__global__ void __launch_bounds__(pdf_maxt<NV>()) k_pair_density_fused(PDArgs<float> a) {
+    using C = cplx<float>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = a.nb, nv = a.nv, nc = a.nc, gc = a.g_per_cta;
+    C* Cks = reinterpret_cast<C*>(smem_raw);       // [nb][nv]
+    C* Ckqs = Cks + (size_t)nb * nv;               // [nb][nc]
+    C* Ys = Ckqs + (size_t)nb * nc;                // [gc][nb][nv]
+    const int k = blockIdx.x;
+    const int g0 = blockIdx.y * gc;
+    const int ngl = min(gc, a.ng - g0);
+    for (int i = threadIdx.x; i < nb * nv; i += blockDim.x) Cks[i] = a.Ck[(size_t)k * nb * nv + i];
+    for (int i = threadIdx.x; i < nb * nc; i += blockDim.x) Ckqs[i] = a.Ckq[(size_t)k * nb * nc + i];
+    const float kk[3] = {a.kpts[3 * k], a.kpts[3 * k + 1], a.kpts[3 * k + 2]};
+    __syncthreads();
+
+    const int ga = threadIdx.x / gc, gl = threadIdx.x - ga * gc;
+    if (ga < a.ngrp && gl < ngl) {
+        const int g = g0 + gl;
+        const float kap[3] = {a.kappa[3 * g], a.kappa[3 * g + 1], a.kappa[3 * g + 2]};
+        const float k2 = kap[0] * kap[0] + kap[1] * kap[1] + kap[2] * kap[2];
+        C Y[4][NV];
+#pragma unroll
+        for (int ca = 0; ca < 4; ++ca)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Y[ca][v] = mk<float>(0, 0);
+        for (int gb = 0; gb < a.ngrp; ++gb) {
+            C blk[4][4];
+            pair_block_vals<float, NCH>(a, ga * a.ngrp + gb, kk, kap, k2, blk);
+            const int mb = a.grp_mask[gb];
+            const int nu0 = a.grp_mu0[gb] - ((mb & 1) ? 0 : 1);
+#pragma unroll
+            for (int cb = 0; cb < 4; ++cb) {
+                if (!(cb == 0 ? (mb & 1) : (mb & 2))) continue;
+                const C* ck = Cks + (size_t)(nu0 + cb) * nv;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (v < nv) {
+                        const C c = ck[v];
+#pragma unroll
+                        for (int ca = 0; ca < 4; ++ca) cfma(Y[ca][v], blk[ca][cb], c);
+                    }
+                }
+            }
+        }
+        const int ma = a.grp_mask[ga];
+        const int mu0 = a.grp_mu0[ga] - ((ma & 1) ? 0 : 1);
+        C* yrow = Ys + (size_t)gl * nb * nv;
+#pragma unroll
+        for (int ca = 0; ca < 4; ++ca) {
+            if (!(ca == 0 ? (ma & 1) : (ma & 2))) continue;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                if (v < nv) yrow[(size_t)(mu0 + ca) * nv + v] = Y[ca][v];
+        }
+    }
+    __syncthreads();
+    const int nvc = nv * nc;
+    for (int i = threadIdx.x; i < ngl * nvc; i += blockDim.x) {
+        const int l = i / nvc, rem = i - l * nvc;
+        const int v = rem / nc, c = rem - v * nc;
+        const C* yv = Ys + (size_t)l * nb * nv + v;
+        C acc = mk<float>(0, 0);
+        for (int mu = 0; mu < nb; ++mu) cfmac(acc, Ckqs[mu * nc + c], yv[(size_t)mu * nv]);
+        __nv_bfloat16 r0, r1, r2, i0, i1, i2;
+        split3_bf16(acc.x, r0, r1, r2);
+        split3_bf16(acc.y, i0, i1, i2);
+        const long long t = ((long long)k * nv + v) * nc + c;
+        const long long o = (long long)(g0 + l) * a.kp2 + t;
+        a.R0[o] = __halves2bfloat162(r0, i0);
+        a.R1[o] = __halves2bfloat162(r1, i1);
+        a.R2[o] = __halves2bfloat162(r2, i2);
     }
 }
 
@@ -309,6 +415,18 @@ template <typename T, int NCH> cudaError_t launch_pd(qcx_ctx* ctx, PDArgs<T>& a,
     if (e != cudaSuccess) return e;
     k_pair_density<T, NCH><<<grid, PD_THREADS, smem, ctx->stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int NCH, int NV> cudaError_t launch_fused(qcx_ctx* ctx, PDArgs<float>& a, size_t smem, dim3 grid, int nthr) {
+    cudaError_t e = set_smem<float>((const void*)k_pair_density_fused<NCH, NV>, smem);
+    if (e != cudaSuccess) return e;
+    k_pair_density_fused<NCH, NV><<<grid, nthr, smem, ctx->stream>>>(a);
+    return cudaGetLastError();
+}
+template <int NCH> cudaError_t launch_fused_nv(qcx_ctx* ctx, PDArgs<float>& a, size_t smem, dim3 grid, int nthr) {
+    if (a.nv <= 4) return launch_fused<NCH, 4>(ctx, a, smem, grid, nthr);
+    if (a.nv <= 8) return launch_fused<NCH, 8>(ctx, a, smem, grid, nthr);
+    return launch_fused<NCH, 16>(ctx, a, smem, grid, nthr);
 }
 
 template <typename T, int NCH> cudaError_t launch_ov(qcx_ctx* ctx, PDArgs<T>& a, size_t smem, int nk) {
@@ -513,7 +631,21 @@ cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precisio
     }
     PDArgs<float> a{};
     fill_common(ctx, a);
-    if (plan_blocks(ctx, a, ctx->nv, &smem)) return cudaErrorInvalidValue;
+    // fused kernel: threads = (G per CTA) x groups, Y = B C_k in registers (nv <= 16)
+    int gcf = 0;
+    size_t smem_f = 0;
+    if (ctx->nv <= 16 && ctx->ngrp <= PDF_MAXT) {
+        const int tmax = ctx->nv <= 4 ? pdf_maxt<4>() : (ctx->nv <= 8 ? pdf_maxt<8>() : pdf_maxt<16>());
+        gcf = std::max(1, std::min(16, tmax / ctx->ngrp));
+        auto need = [&](int gc) {
+            return sizeof(cplx<float>) * ((size_t)ctx->nb * ctx->nv + (size_t)ctx->nb * ctx->nc +
+                                          (size_t)gc * ctx->nb * ctx->nv);
+        };
+        while (gcf > 1 && need(gcf) > 200 * 1024) --gcf;
+        smem_f = need(gcf);
+        if (smem_f > 200 * 1024) gcf = 0;
+    }
+    if (!gcf && plan_blocks(ctx, a, ctx->nv, &smem)) return cudaErrorInvalidValue;
     a.nv = ctx->nv;
     a.nc = ctx->nc;
     a.nk = ctx->nk;
@@ -531,6 +663,16 @@ cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precisio
     a.R1 = a.R0 + (size_t)s.ngp * (s.kp / 2);
     a.R2 = a.R1 + (size_t)s.ngp * (s.kp / 2);
     a.kp2 = s.kp / 2;
+    if (gcf) {
+        a.g_per_cta = gcf;
+        const dim3 gridf(ctx->nk, (s.ng + gcf - 1) / gcf);
+        const int nthr = gcf * ctx->ngrp;
+        switch (ctx->nchar) {
+            case 1: return launch_fused_nv<1>(ctx, a, smem_f, gridf, nthr);
+            case 2: return launch_fused_nv<2>(ctx, a, smem_f, gridf, nthr);
+            default: return launch_fused_nv<4>(ctx, a, smem_f, gridf, nthr);
+        }
+    }
     switch (ctx->nchar) {
         case 1: return launch_pd<float, 1>(ctx, a, smem, grid);
         case 2: return launch_pd<float, 2>(ctx, a, smem, grid);
