@@ -29,6 +29,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one k_chi0_tc launch over 1 q x 200 w of the mid workload, from one ncu capture
+# of `bench.py --profile-case mid200` (profiles/k_chi0_tc_traffic_mid_1q200w.md); to be retaken whenever the
+# kernel changes.
+CHI0_TRAFFIC_BYTES = 923490816 + 182294016
 METRIC = "eps^-1 (q,w) blocks/s vs FP64 plain GPU path at <=1e-4 rel err; tensor-pipe %"
 WORKLOAD = ("mid: diamond a=5.43 A, 12 sp shells/atom (N_b=96), 8x8x8 k, N_v=4, N_c=32 (N_t=65536), "
             "N_G=181, 50 q x 200 w on 0-60 eV, eta=0.1 eV")
@@ -328,7 +332,10 @@ def run_ours(args, ws, rank, local):
                                        "FP64 diagonal correction; rate FP64",
                           "parallelism": f"q shards x {ws}"},
                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": None,
+                            "frac": achieved / peak, "traffic": CHI0_TRAFFIC_BYTES,
+                            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_chi0_tc "
+                                              "launch of 1 q x 200 w (the launch this step times), "
+                                              "profiles/k_chi0_tc_traffic_mid_1q200w.md",
                             "kernel": "k_chi0_tc", "flops_per_launch": pref_flops,
                             "avg_launch_ms": chi_avg,
                             "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)"},
@@ -490,8 +497,9 @@ def run_profile_case_mlp():
     print("profile case done")
 
 
-def run_profile_case():
-    """1 q x 50 w of the mid workload through the mixed path, twice."""
+def run_profile_case(nw=50):
+    """1 q x nw w of the mid workload through the mixed path, twice (nw = 200 is the
+    launch configuration the benchmark step times)."""
     import torch
 
     import synth
@@ -499,7 +507,7 @@ def run_profile_case():
     from paper_2603_12326_gb300.build import build
     build()
     ctx = qcx.Context(0)
-    prob = synth.make_mid(nq=1, nw=50)
+    prob = synth.make_mid(nq=1, nw=nw)
     states.load_problem(ctx, prob)
     for _ in range(2):
         ctx.pair_density(0, prob.G_int, QCX_MIXED)
@@ -519,7 +527,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-correction leg")
-    ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "batch", "mlp"],
+    ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "mid200", "batch", "mlp"],
                     help="small case for profilers, no report: mid = 1 q x 50 w of the mid workload, 2 passes; "
                          "batch = the uneven workload once; mlp = one gradient and one prediction")
     args = ap.parse_args()
@@ -533,6 +541,8 @@ def main():
         dist.init_process_group(backend)
     if args.profile_case == "mid":
         run_profile_case()
+    elif args.profile_case == "mid200":
+        run_profile_case(200)
     elif args.profile_case == "batch":
         run_profile_case_batch()
     elif args.profile_case == "mlp":

@@ -172,13 +172,23 @@ qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, q
  *   out_diag_inv[nw][ng]   [eps^-1]_GG                     (Eq. (eps_LFE))
  *   out_eps_diag[nw][ng]   eps_GG                          (Eq. (eps_noLFE))
  *   out_resid[nw]          QCX_MIXED: max_G |correction| / |[eps^-1]_GG| of the
- *                          FP64 correction for blocks with kappa_1 > 1e3 (the
+ *                          FP64 correction for blocks with kappa_1 above the
+ *                          threshold of qcx_set_refine_threshold (the
  *                          ill-conditioned ones), 0 for the others; 0 for QCX_FP64.
  * and keeps the loss tables of iq in the context.
  * Errors: QCX_ERR_STATE, QCX_ERR_SINGULAR (zero pivot in some block; the
  * other blocks are valid), QCX_ERR_ALLOC, QCX_ERR_CUDA. */
 qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out_diag_inv,
                           qcx_c64* out_eps_diag, double* out_resid);
+
+/* Mixed path of qcx_invert_eps: blocks whose condition estimate
+ * kappa_1 = |eps|_1 |X|_1 (X the FP32 inverse) exceeds kappa1 get the FP64
+ * correction of the diagonal (the precision plan's FP64 residual near the
+ * plasmon, where eps is ill-conditioned); the others take L_LFE as the
+ * diagonal of X B X^H with B = (eps - eps^H)/(2i), formed from the FP64 eps.
+ * Default 1e4; 0 corrects every block.  Applies to later qcx_invert_eps calls
+ * of this context.  Errors: QCX_ERR_ARG (ctx NULL, kappa1 negative or NaN). */
+qcx_status qcx_set_refine_threshold(qcx_ctx* ctx, double kappa1);
 
 /* Loss functions of q number iq (Eq. (dynamic_structure_factor)):
  *   out_L_lfe[nw][ng]   = -Im [eps^-1]_GG   (with local fields)

@@ -145,6 +145,7 @@ struct qcx_ctx {
     unsigned long long gen = 0;    // bumped whenever basis or states change
     BatchPlan* batch = nullptr;    // cached plan (and captured graph) of the last batched solve
     int batch_tune = 1;            // autotune the batch tiling when a new plan is built
+    double kappa_refine = 1.0e4;   // mixed inverse: FP64 diagonal correction above this kappa_1
     MlpState* mlp = nullptr;       // surrogate network (parameters, Adam moments, work buffers)
 
     ~qcx_ctx();

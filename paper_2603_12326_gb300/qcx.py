@@ -49,6 +49,7 @@ _SIGS = {
     "qcx_pair_density": (I, [P, I, I, P, I, P]),
     "qcx_chi0": (I, [P, I, I, P, D, I, P]),
     "qcx_invert_eps": (I, [P, I, I, P, P, P]),
+    "qcx_set_refine_threshold": (I, [P, D]),
     "qcx_loss_function": (I, [P, I, P, P]),
     "qcx_bin_loss": (I, [P, I, P, I, I, P, P, P]),
     "qcx_rate": (I, [P, I, P, I, P, P, ct.POINTER(HaloParams), P, I, P]),
@@ -232,6 +233,9 @@ class Context:
             return d, e, r
         self._check(qcx_invert_eps(self.h, iq, prec, None, None, None))
         return None
+
+    def set_refine_threshold(self, kappa1):
+        self._check(qcx_set_refine_threshold(self.h, float(kappa1)))
 
     def loss_function(self, iq, prec=QCX_FP64, out_lfe=None, out_nolfe=None):
         nw, ng = self._nw[prec], self._ng[prec]

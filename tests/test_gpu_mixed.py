@@ -1,18 +1,20 @@
-"""Mixed-precision GPU path (FP32 pair densities stored as BF16 hi/lo pairs,
-split-BF16 tcgen05 chi0 with FP32 accumulation, FP32 Gauss-Jordan inverse with
-an FP64 diagonal correction) vs the FP64 CPU oracle.
+"""Mixed-precision GPU path (FP32 pair densities stored as three BF16 terms,
+split-BF16 tcgen05 chi0 with FP32 accumulation, FP32 Gauss-Jordan inverse, the
+FP64 diagonal correction for ill-conditioned blocks and the loss as a quadratic
+form for the others) vs the FP64 CPU oracle.
 
-Tolerances follow from the arithmetic: x = hi + lo in BF16 represents x to
-2^-16 (1.5e-5) relative; a product hi*hi + hi*lo + lo*hi misses at most
-3 * 2^-16 of |ab|; sums over transitions average these errors.  The loss
-functions must stay within 1e-4 relative wherever they exceed 1e-3 of their
-per-q maximum (the bar the method is held to)."""
+Tolerances follow from the arithmetic: three BF16 terms represent x to 2^-24
+relative and the six products kept miss terms of that order, so chi0 carries
+the FP32 rounding of its sums (5e-5 bound); the inverse amplifies eps errors by
+its condition number.  The loss functions must stay within 1e-4 relative
+wherever they exceed 1e-3 of their per-q maximum (the bar the method is held
+to)."""
 import numpy as np
 import pytest
 
 import synth
 from oracle import rpa
-from paper_2603_12326_gb300 import QCX_MIXED
+from paper_2603_12326_gb300 import QCX_MIXED, qcx
 from tests.gpu_util import context, rel, rel_spectrum, set_oracle_states
 
 pytestmark = pytest.mark.gpu
@@ -81,3 +83,28 @@ def test_split_g_range_mixed(ctx):
     set_oracle_states(ctx, p, [0], Ck, [Ckq])
     rho, chi, dinv, ed, resid, L1, L2 = _run(ctx, 0, p)
     _check(o, rho, chi, dinv, ed, L1, L2)
+
+
+def test_fp64_correction_of_every_block(ctx):
+    """Threshold 0: every block of a small-workload q goes through the FP64
+    diagonal correction (the path the ill-conditioned blocks take); the result
+    still matches the oracle and every block reports its correction."""
+    p = synth.make_small()
+    Ck, Ckq = rpa.states(p, 6)
+    o = rpa.solve_q(p, 6, Ck, Ckq)
+    set_oracle_states(ctx, p, [6], Ck, [Ckq])
+    for bad in (-1.0, float("nan")):
+        with pytest.raises(qcx.QcxError) as ei:
+            ctx.set_refine_threshold(bad)
+        assert ei.value.status == 1
+    ctx.set_refine_threshold(0.0)
+    try:
+        rho, chi, dinv, ed, resid, L1, L2 = _run(ctx, 0, p)
+    finally:
+        ctx.set_refine_threshold(1.0e4)
+    assert np.all(resid[1:] > 0.0) and np.all(resid < 1e-4)
+    _check(o, rho, chi, dinv, ed, L1, L2)
+    # the default threshold gives the same loss within the tolerance
+    d2, _, r2 = ctx.invert_eps(0, QCX_MIXED)
+    L1b, _ = ctx.loss_function(0, QCX_MIXED)
+    assert rel_spectrum(L1b, o["L_lfe"]) < 1e-4
