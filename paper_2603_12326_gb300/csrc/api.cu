@@ -281,8 +281,11 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
         s.iq = -1;
         s.have_rho = s.have_eps = false;
     }
-    for (auto* l : ctx->loss) delete l;
-    ctx->loss.assign(nq, nullptr);
+    // keep the tables' device buffers for the new states (no allocation in a steady loop)
+    for (size_t i = nq; i < ctx->loss.size(); ++i) delete ctx->loss[i];
+    ctx->loss.resize(nq, nullptr);
+    for (auto* l : ctx->loss)
+        if (l) l->valid = false;
     return QCX_OK;
 }
 
@@ -333,10 +336,7 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
     }
     s.iq = iq;
     s.have_rho = true;
-    if (ctx->loss[iq]) {
-        delete ctx->loss[iq];
-        ctx->loss[iq] = nullptr;
-    }
+    if (ctx->loss[iq]) ctx->loss[iq]->valid = false;
     return QCX_OK;
 }
 
@@ -417,6 +417,7 @@ qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out
     CUDA_OR_FAIL(qcx_launch_invert(ctx, s, prec, lt->L.as<double>()), "invert kernel");
     lt->w.resize(nw);
     CUDA_OR_FAIL(cudaMemcpyAsync(lt->w.data(), s.w.p, nw * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "w");
+    lt->valid = true;
     std::vector<int> flags(nw);
     CUDA_OR_FAIL(cudaMemcpyAsync(flags.data(), s.flags.p, nw * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
                  "flags");
@@ -433,7 +434,8 @@ qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out
 qcx_status qcx_loss_function(qcx_ctx* ctx, int iq, double* out_L_lfe, double* out_L_nolfe) {
     if (!ctx) return QCX_ERR_ARG;
     ctx->err.clear();
-    if (iq < 0 || iq >= ctx->nq || !ctx->loss[iq]) return ctx->fail(QCX_ERR_STATE, "loss: q not inverted");
+    if (iq < 0 || iq >= ctx->nq || !ctx->loss[iq] || !ctx->loss[iq]->valid)
+        return ctx->fail(QCX_ERR_STATE, "loss: q not inverted");
     cudaSetDevice(ctx->device);
     LossTab* lt = ctx->loss[iq];
     const size_t n = (size_t)lt->nw * lt->ng * sizeof(double);
@@ -461,7 +463,8 @@ qcx_status qcx_bin_loss(qcx_ctx* ctx, int nsel, const int* iq_list, int which, i
     const std::vector<double>* wref = nullptr;
     for (int i = 0; i < nsel; ++i) {
         const int iq = iqs[i];
-        if (iq < 0 || iq >= ctx->nq || !ctx->loss[iq]) return ctx->fail(QCX_ERR_STATE, "bin_loss: q not inverted");
+        if (iq < 0 || iq >= ctx->nq || !ctx->loss[iq] || !ctx->loss[iq]->valid)
+            return ctx->fail(QCX_ERR_STATE, "bin_loss: q not inverted");
         LossTab* lt = ctx->loss[iq];
         if (nw < 0) {
             nw = lt->nw;

@@ -64,6 +64,7 @@ struct QSlot {
 
 // Loss tables kept per q after qcx_invert_eps.
 struct LossTab {
+    bool valid = false;        // holds the tables of the current states; buffers are kept when invalidated
     int ng = 0, nw = 0;
     DevBuf L;                  // [2][nw][ng] double: LFE then noLFE
     DevBuf qmag;               // [ng] double |q+G|
