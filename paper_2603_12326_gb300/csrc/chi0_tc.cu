@@ -360,7 +360,9 @@ __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, co
             const int vv = rem / nc, c = rem - vv * nc;
             const double dE = Ekq[k * nc + c] - Ek[k * nv + vv];
             const double x1 = w[iw] - dE, x2 = w[iw] + dE;
-            const double d1 = 1.0 / (x1 * x1 + eta * eta), d2 = 1.0 / (x2 * x2 + eta * eta);
+            const double n1 = x1 * x1 + eta * eta, n2 = x2 * x2 + eta * eta;
+            const double r = 1.0 / (n1 * n2);         // one FP64 division for both denominators
+            const double d1 = n2 * r, d2 = n1 * r;
             v = make_float2((float)(x1 * d1 - x2 * d2), (float)(eta * (d2 - d1)));
         }
         W[i] = v;

@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(INV_THREADS) k_gauss_jordan(InvArgs<T> a, int 
 
 // Mixed path, N_G <= GJC_MAXN: the same elimination with the matrix resident
 // in shared memory, split by columns over a cluster of GJC_CS CTAs (a 181 x 181
-// FP32 complex matrix is 262 KB, more than one CTA holds).  Step k: the CTA
+// FP32 complex matrix is 262 KB, more than one CTA holds; with four CTAs of
+// 74 KB, three clusters' CTAs share an SM and hide each other's barriers).  Step k: the CTA
 // owning column k picks the pivot row and publishes the row index, the pivot
 // and column k after the row exchange (the multipliers) in its shared memory;
 // after one cluster barrier the others read them through distributed shared
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(INV_THREADS) k_gauss_jordan(InvArgs<T> a, int 
 // in its own columns.  The published values alternate between two slots, so
 // the barrier of the next step also orders their reuse.  Warps take rows,
 // lanes take columns.
-constexpr int GJC_CS = 2;
-constexpr int GJC_THREADS = 512;
+constexpr int GJC_CS = 4;
+constexpr int GJC_THREADS = 256;
 constexpr int GJC_MAXN = 192;
 constexpr int GJC_WARPS = GJC_THREADS / 32;
 
