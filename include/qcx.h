@@ -62,7 +62,9 @@ typedef enum {
                        tcgen05 products (the six of order <= 2) with the FP32 tensor-core sums
                        promoted every two K stages and accumulated in FP64; eps stored in FP64;
                        FP32 Gauss-Jordan inverse with an FP64 residual correction of the diagonal
-                       for ill-conditioned blocks (kappa_1 > 1e3); dE and w -+ dE in FP64       */
+                       for ill-conditioned blocks (kappa_1 above qcx_set_refine_threshold, 1e4
+                       by default) and the other blocks' loss as a quadratic form of the FP64
+                       matrix's anti-Hermitian part; dE and w -+ dE in FP64                    */
 } qcx_precision;
 
 typedef struct { double re, im; } qcx_c64;
@@ -146,8 +148,8 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
 /* Pair densities for q number iq and the G set G_int[ng][3]
  * (Eq. (RPA) matrix elements; closed-form Gaussian-product integrals with
  * the lattice sum done as separable one-dimensional sums).  The result is
- * kept in the context (FP64 for QCX_FP64; FP32 values stored as BF16
- * hi/lo pairs for QCX_MIXED) and, if out_rho != NULL, also written to
+ * kept in the context (FP64 for QCX_FP64; FP32 values stored as three
+ * BF16 terms for QCX_MIXED) and, if out_rho != NULL, also written to
  * out_rho[nt][ng] (complex double).  Starts a new q: the context's chi0,
  * eps and loss tables for other q are untouched; those for iq are reset.
  * Errors: QCX_ERR_STATE (no states), QCX_ERR_ARG (iq, ng < 1, ng > 4096),

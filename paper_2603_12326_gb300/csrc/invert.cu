@@ -618,7 +618,7 @@ cudaError_t qcx_launch_invert(qcx_ctx* ctx, QSlot& s, qcx_precision prec, double
     a.L = d_loss_out;
     a.flags = s.flags.as<int>();
     if (n <= GJC_MAXN) {
-        // the matrix stays in the shared memory of a 2-CTA cluster
+        // the matrix stays in the shared memory of a GJC_CS-CTA cluster
         const size_t smem = gjc_smem(n);
         e = cudaFuncSetAttribute((const void*)k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
