@@ -108,6 +108,12 @@ def _barrier_max(ws, value):
     return float(t.item())
 
 
+def _weak_value(nq, nw, steps, ws, ms_max):
+    """Whole-job blocks/s: every rank processes its own nq x nw blocks per step;
+    the time is the slowest rank's."""
+    return nq * nw * steps * ws / (ms_max / 1e3)
+
+
 def _barrier(ws):
     if ws > 1:
         import torch.distributed as dist
@@ -242,8 +248,7 @@ def run_ours(args, ws, rank, local):
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     ms = _barrier_max(ws, ms)
-    blocks = nq * nw * args.steps * ws
-    value = blocks / (ms / 1e3)
+    value = _weak_value(nq, nw, args.steps, ws, ms)
     chi_ms = [a.elapsed_time(b) for a, b in chi_events]
     chi_avg = float(np.mean(chi_ms))
     peaks = _peaks()
