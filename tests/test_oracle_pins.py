@@ -396,6 +396,51 @@ def test_rate_scalings_and_form_factor_limits():
     assert np.isclose(spec.sum(), np.sum(r1[wev >= ph.w_gap_eV]) * dw, rtol=1e-13)
 
 
+def test_rate_units_against_an_si_evaluation():
+    """The natural-unit rate (eV, hbar = c = 1; Eq. (general_rate) with
+    Eq. (dynamic_structure_factor)) against the same formula written in SI
+    units with scipy's constants: a rate density with dimensions
+    kg m^5 s^-3 carries the factor 1/(hbar^3 c) to become events per
+    (kg s J).  Momenta in bohr^-1 are hbar q / a_0, frequencies in Hartree are
+    w E_h, masses in eV are m e / c^2; heavy and light mediators."""
+    sc = pytest.importorskip("scipy.constants")
+    hbar, c, e = sc.hbar, sc.c, sc.e
+    a0 = sc.physical_constants["Bohr radius"][0]
+    Eh = sc.physical_constants["Hartree energy"][0]
+    me = sc.m_e
+    yr = 365.25 * 24 * 3600.0
+    qb = np.linspace(0.4, 3.2, 15)                  # bohr^-1
+    w = np.linspace(0.0, 30.0, 31) / rate.HARTREE_EV
+    rng = np.random.default_rng(5)
+    L = rng.uniform(0.0, 0.5, (15, 31))
+    for m_med in (-1.0, 0.0):
+        ph = rate.HaloParams(m_chi_eV=5e7, m_med_eV=m_med)
+        got = rate.dR_dw(qb, w, L, ph)                                   # events/(kg yr eV)
+        m_chi = ph.m_chi_eV * e / c ** 2                                  # kg
+        mu = m_chi * me / (m_chi + me)
+        n_chi = ph.rho_chi_GeV_cm3 * 1e9 / ph.m_chi_eV * 1e6              # m^-3
+        rho_T = ph.rho_T_g_cm3 * 1e3                                      # kg m^-3
+        sigma = ph.sigma_e_cm2 * 1e-4                                     # m^2
+        q = hbar * qb / a0                                                # kg m s^-1
+        want = np.zeros(w.shape[0])
+        for iw, wh in enumerate(w):
+            E = wh * Eh                                                    # J
+            g = np.zeros(q.shape[0])
+            for iq, qv in enumerate(q):
+                vmin = qv / (2 * m_chi) + E / qv                           # m s^-1
+                eta = rate.eta_shm(vmin / c, ph.v0_kms * 1e3 / c, ph.vesc_kms * 1e3 / c, ph.vE_kms * 1e3 / c) / c
+                F2 = 1.0 if m_med < 0 else (sc.alpha * me * c / qv) ** 4
+                g[iq] = qv ** 3 * F2 * L[iq, iw] * eta
+            si = n_chi / rho_T * sigma / (8 * np.pi ** 2 * sc.alpha * mu ** 2) * np.trapezoid(g, q) / (hbar ** 3 * c)
+            want[iw] = si * yr * e                                         # events/(kg yr eV)
+        nz = want > 0
+        assert nz.sum() > 10
+        # scipy's constants (CODATA 2022) differ from the oracle's (2018) by ~1e-9; near the velocity cutoff
+        # eta's steep fall magnifies that to ~2e-7, far below what a wrong power of hbar or c would give
+        assert np.allclose(got[nz], want[nz], rtol=1e-6, atol=0)
+        assert np.all(got[~nz] == 0)
+
+
 def test_kinetic_textbook_values():
     """The kinetic matrix used by the f-sum pin: for a tight isolated
     normalised s Gaussian <T> = 3a/2, for p it is 5a/2; for two s Gaussians
