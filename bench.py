@@ -209,10 +209,21 @@ def run_ours(args, ws, rank, local):
     pref_flops = 8.0 * nt * ng * ng * nw          # algorithmic chi0 flops per q (one launch)
 
     chi_events = []
+    pd_events = []
+    # algorithmic bytes of one pair-density launch: the FP32 coefficients read once, the three BF16 planes of
+    # rho written once
+    pd_bytes = 8.0 * prob.nk * prob.basis.nbasis * (prob.nv + prob.nc) + 12.0 * nt * ng
 
     def step(record=False):
         for iq in range(nq):
+            if record:
+                p0 = torch.cuda.Event(enable_timing=True)
+                p1 = torch.cuda.Event(enable_timing=True)
+                p0.record(stream)
             ctx.pair_density(iq, G, QCX_MIXED)
+            if record:
+                p1.record(stream)
+                pd_events.append((p0, p1))
             if record:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -251,6 +262,7 @@ def run_ours(args, ws, rank, local):
     value = _weak_value(nq, nw, args.steps, ws, ms)
     chi_ms = [a.elapsed_time(b) for a, b in chi_events]
     chi_avg = float(np.mean(chi_ms))
+    pd_avg = float(np.mean([a.elapsed_time(b) for a, b in pd_events]))
     peaks = _peaks()
     achieved = pref_flops / (chi_avg / 1e3) / 1e12
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -344,6 +356,12 @@ def run_ours(args, ws, rank, local):
                             "kernel": "k_chi0_tc", "flops_per_launch": pref_flops,
                             "avg_launch_ms": chi_avg,
                             "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)"},
+               "pair_density": {"kernel": "k_pair_density_fused", "avg_launch_ms": pd_avg, "bound": "alu",
+                                "algorithmic_bytes": pd_bytes, "achieved_GBs": pd_bytes / (pd_avg / 1e3) / 1e9,
+                                "hbm_peak_GBs": peaks.get("hbm_gbs", 6800.0),
+                                "hbm_frac": pd_bytes / (pd_avg / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                                "note": "FP32 lattice sums of the Gaussian-pair blocks bound it, not HBM "
+                                        "(profiles/k_pair_density_fused_mid_1q.md)"},
                "e2e": {"value": nq * nw * ws / (e2e_ms / 1e3), "unit": "blocks/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
                "fp64_gpu": {"value": fp64_value, "unit": "blocks/s",
