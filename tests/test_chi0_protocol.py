@@ -1,6 +1,8 @@
-"""The mbarrier protocol of the tensor-core chi0 kernel, checked on the CPU.
+"""The mbarrier protocol of the tensor-core chi0 kernels, checked on the CPU.
 
-A random-schedule model of k_chi0_tc's roles: the TMA producer, the A-operand
+A random-schedule model of the roles of k_chi0_tc (one tile per CTA) and of
+the persistent k_chi0_tc_batch (a list of tiles per CTA, stage and window
+counters running on across tiles): the TMA producer, the A-operand
 warps (which also drain the accumulators), two MMA issuers on alternate
 accumulation windows, copies that land in any order and MMAs that complete in
 issue order.  Barriers follow the mbarrier phase rule (a wait on parity p
@@ -18,12 +20,12 @@ import re
 
 import pytest
 
-SRC = os.path.join(os.path.dirname(__file__), "..", "paper_2603_12326_gb300", "csrc", "chi0_tc.cu")
+CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2603_12326_gb300", "csrc")
 
 
-def _constant(name):
-    m = re.search(r"constexpr int %s = (\d+);" % name, open(SRC).read())
-    assert m, name
+def _constant(name, src="chi0_tc.cu"):
+    m = re.search(r"constexpr int %s = (\d+);" % name, open(os.path.join(CSRC, src)).read())
+    assert m, (src, name)
     return int(m.group(1))
 
 
@@ -38,7 +40,7 @@ class _Bar:
         return (self.done & 1) != parity
 
 
-def _run(kstages, nstage, promote, seed):
+def _run(kstages, nstage, promote, seed, ntile=1):
     rnd = random.Random(seed)
     full_b = [_Bar() for _ in range(nstage)]
     full_a = [_Bar() for _ in range(nstage)]
@@ -55,47 +57,61 @@ def _run(kstages, nstage, promote, seed):
         if not event_happened():
             errors.append("early pass: " + what)
 
+    ntot = ntile * kstages                       # stages of all tiles of the CTA, in order
+
     def producer():
-        for it in range(kstages):
-            s, ph = it % nstage, (it // nstage) & 1
-            yield from wait(empty[s], ph ^ 1, lambda it=it: it < nstage or (it - nstage) in mma_done,
-                            "stage %d free" % it)
-            copies.append((it, s))
+        for gs in range(ntot):
+            s, ph = gs % nstage, (gs // nstage) & 1
+            yield from wait(empty[s], ph ^ 1, lambda gs=gs: gs < nstage or (gs - nstage) in mma_done,
+                            "stage %d free" % gs)
+            copies.append((gs, s))
 
     def a_warps():
-        def drain(wd):
-            yield from wait(acc_full[wd & 1], (wd >> 1) & 1, lambda: ("win", wd) in mma_done, "window %d" % wd)
-            drain_done.add(wd)
-            drained[wd & 1].arrive()
+        def drain(gw):
+            yield from wait(acc_full[gw & 1], (gw >> 1) & 1, lambda: ("win", gw) in mma_done, "window %d" % gw)
+            drain_done.add(gw)
+            drained[gw & 1].arrive()
 
-        for it in range(kstages):
-            s, ph = it % nstage, (it // nstage) & 1
-            yield from wait(full_b[s], ph, lambda it=it: it in landed, "copy %d" % it)
-            if it >= nstage and (it - nstage) not in mma_done:
-                errors.append("A tile %d overwritten under its MMAs" % it)
-            gen_done.add(it)
-            full_a[s].arrive()
-            if it % promote == promote - 1 and it >= promote:
-                yield from drain(it // promote - 1)
-        if nwin >= 2 and (kstages - 1) % promote != promote - 1:
-            yield from drain(nwin - 2)
-        yield from drain(nwin - 1)
+        for lt in range(ntile):
+            for it in range(kstages):
+                gs = lt * kstages + it
+                s, ph = gs % nstage, (gs // nstage) & 1
+                yield from wait(full_b[s], ph, lambda gs=gs: gs in landed, "copy %d" % gs)
+                if gs >= nstage and (gs - nstage) not in mma_done:
+                    errors.append("A tile %d overwritten under its MMAs" % gs)
+                gen_done.add(gs)
+                full_a[s].arrive()
+                # drain the previous window after the last stage of a window; at the tile's end the rest
+                wd0, wd1 = nwin, -1
+                if it % promote == promote - 1 and it >= promote:
+                    wd0 = wd1 = it // promote - 1
+                if it + 1 == kstages:
+                    wd0 = min(wd0, it // promote - 1 if (it % promote == promote - 1 and it >= promote)
+                              else max(nwin - 2, 0))
+                    wd1 = nwin - 1
+                for wd in range(wd0, wd1 + 1):
+                    yield from drain(lt * nwin + wd)
 
     def issuer(par):
-        for win in range(par, nwin, 2):
-            b = win & 1
-            if win >= 2:
-                yield from wait(drained[b], ((win - 2) >> 1) & 1, lambda w=win: (w - 2) in drain_done,
-                                "buffer of window %d drained" % win)
-            for it in range(win * promote, min((win + 1) * promote, kstages)):
-                s = it % nstage
-                yield from wait(full_a[s], (it // nstage) & 1, lambda it=it: it in gen_done, "A tile %d" % it)
-                if it not in landed:
-                    errors.append("MMA %d before its copy landed" % it)
-                mmas.append((it, [empty[s]]))
+        for lt in range(ntile):
+            for wd in range(nwin):
+                gw = lt * nwin + wd
+                if (gw & 1) != par:
+                    continue
+                b = gw & 1
+                if gw >= 2:
+                    yield from wait(drained[b], ((gw - 2) >> 1) & 1, lambda g=gw: (g - 2) in drain_done,
+                                    "buffer of window %d drained" % gw)
+                for it in range(wd * promote, min((wd + 1) * promote, kstages)):
+                    gs = lt * kstages + it
+                    s = gs % nstage
+                    yield from wait(full_a[s], (gs // nstage) & 1, lambda gs=gs: gs in gen_done, "A tile %d" % gs)
+                    if gs not in landed:
+                        errors.append("MMA %d before its copy landed" % gs)
+                    mmas.append((gs, [empty[s]]))
+                    yield
+                mmas.append((("win", gw), [acc_full[b]]))
                 yield
-            mmas.append((("win", win), [acc_full[b]]))
-            yield
 
     actors = [producer(), a_warps(), issuer(0), issuer(1)]
     alive = [True] * len(actors)
@@ -131,6 +147,18 @@ def test_kernel_protocol_holds_under_random_schedules(kstages):
         assert not errors, (nstage, promote, kstages, seed, errors[:3])
         nwin = (kstages + promote - 1) // promote
         assert counts == (kstages, nwin)
+
+
+@pytest.mark.parametrize("kstages,ntile", [(1, 5), (2, 4), (3, 3), (5, 3), (8, 2), (13, 3)])
+def test_batch_kernel_protocol_across_tiles(kstages, ntile):
+    """The persistent batch kernel runs the same roles over a list of tiles with
+    the stage and window counters continuing across tiles."""
+    nstage, promote = _constant("NSTAGE", "chi0_tc_batch.cu"), _constant("PROMOTE", "chi0_tc_batch.cu")
+    for seed in range(40):
+        errors, counts = _run(kstages, nstage, promote, seed, ntile=ntile)
+        assert not errors, (kstages, ntile, seed, errors[:3])
+        nwin = (kstages + promote - 1) // promote
+        assert counts == (kstages * ntile, nwin * ntile)
 
 
 def test_two_stage_ring_is_caught():
