@@ -425,7 +425,7 @@ def batched_leg(stream, reps=10):
 
 def surrogate_leg(stream):
     """The learned correction on its own workload (110 q of the mid workload,
-    200 w each): heads by the mixed Dyson route, training on 100 q, judged on
+    200 w each): heads by the mixed Dyson route, training on 100 q, evaluated on
     the 10 others; then the surrogate route (accept where sigma < 1e-2, 5 %
     spot check, Dyson fallback) on the held-out q."""
     import torch

@@ -274,7 +274,7 @@ qcx_status qcx_batch_autotune(qcx_ctx* ctx, int enable);
  * of one (q, w) head to (mu, s): mu estimates y = log(L_LFE / L_noLFE) and
  * s = log sigma^2 its uncertainty, so that L_LFE ~ L_noLFE e^mu can stand in
  * for the Dyson route where sigma is small, with the Dyson route (the heads
- * of qcx_solve_batch or of qcx_invert_eps) as fallback and judge.
+ * of qcx_solve_batch or of qcx_invert_eps) as fallback and check.
  * Parameters: one FP32 vector of QCX_MLP_NPARAM = 34178 entries, per layer
  * W [out][in] row-major then b [out] (layers 6->128, 128->128, 128->128,
  * 128->2).  Compute copies of the weight matrices are BF16; biases,

@@ -1,6 +1,6 @@
 """The learned local-field correction on its own workload: 110 q of the
 mid-size workload (200 w each), heads from the mixed Dyson route; the network
-is trained on 100 q and judged on 10 held-out q.
+is trained on 100 q and evaluated on 10 held-out q.
 
 What it gains over the method without it: the no-LFE method takes
 L_LFE = L_noLFE (log ratio 0); the trained network must predict the held-out
