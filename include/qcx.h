@@ -161,9 +161,11 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
  * (Eq. (RPA)), followed in the same kernel by the Dyson step
  * eps = 1 - v^1/2 chi0 v^1/2, kept in the context.  Needs
  * qcx_pair_density(iq) in the same precision.  out_chi0[nw][ng][ng]
- * (row G, column G') is optional.  Errors: QCX_ERR_STATE, QCX_ERR_ARG
- * (nw < 1, eta <= 0, non-finite w), QCX_ERR_ALLOC, QCX_ERR_CUDA,
- * QCX_ERR_TIMEOUT (a pipeline wait gave up; results are invalid). */
+ * (row G, column G') is optional.  The loss tables of iq from an earlier
+ * qcx_invert_eps are reset (they belong to the previous chi0).
+ * Errors: QCX_ERR_STATE, QCX_ERR_ARG (nw < 1, eta <= 0, non-finite w),
+ * QCX_ERR_ALLOC, QCX_ERR_CUDA, QCX_ERR_TIMEOUT (a pipeline wait gave up;
+ * results are invalid). */
 qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, qcx_precision prec,
                     qcx_c64* out_chi0);
 
@@ -195,7 +197,9 @@ qcx_status qcx_set_refine_threshold(qcx_ctx* ctx, double kappa1);
 /* Loss functions of q number iq (Eq. (dynamic_structure_factor)):
  *   out_L_lfe[nw][ng]   = -Im [eps^-1]_GG   (with local fields)
  *   out_L_nolfe[nw][ng] = -Im (1/eps_GG)    (without)
- * Needs qcx_invert_eps(iq).  Errors: QCX_ERR_STATE, QCX_ERR_CUDA. */
+ * Needs qcx_invert_eps(iq) after the last qcx_pair_density(iq) and
+ * qcx_chi0(iq) (and after the last qcx_set_states); the tables stay until
+ * then.  Errors: QCX_ERR_STATE (tables not current), QCX_ERR_CUDA. */
 qcx_status qcx_loss_function(qcx_ctx* ctx, int iq, double* out_L_lfe, double* out_L_nolfe);
 
 /* Average the stored loss tables of the listed q over |q+G| bins

@@ -355,6 +355,7 @@ qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, q
     s.nw = nw;
     s.eta = eta;
     s.have_eps = false;
+    if (ctx->loss[iq]) ctx->loss[iq]->valid = false;     // the tables of iq belong to the previous chi0
     const int ng = s.ng;
     CUDA_OR_FAIL(s.w.ensure(sizeof(double) * nw), "alloc");
     CUDA_OR_FAIL(cudaMemcpyAsync(s.w.p, wh.data(), sizeof(double) * nw, cudaMemcpyHostToDevice, ctx->stream), "copy w");

@@ -139,3 +139,52 @@ def test_call_order_and_argument_errors(ctx):
     ctx.invert_eps(0, QCX_FP64)
     L1, L2 = ctx.loss_function(0, QCX_FP64)
     assert np.all(np.isfinite(L1))
+
+
+def test_loss_tables_follow_the_computation(ctx):
+    """The loss tables of a q are readable only after qcx_invert_eps on the
+    current pair densities, chi0 and states; recomputing any of them resets the
+    tables of that q (their device buffers are kept and reused).  Empty G and
+    frequency lists are argument errors."""
+    p = synth.make_tiny(seed=5, nq=2, nw=6)
+    st = [rpa.states(p, iq) for iq in range(2)]
+    set_oracle_states(ctx, p, [0, 1], st[0][0], [s[1] for s in st])
+    edges = np.linspace(0.0, 10.0, 11)
+    for iq in range(2):
+        ctx.pair_density(iq, p.G_int, QCX_FP64)
+        ctx.chi0(iq, p.w, p.eta, QCX_FP64)
+        ctx.invert_eps(iq, QCX_FP64)
+    L0, _ = ctx.loss_function(0, QCX_FP64)
+    ctx.bin_loss([0, 1], 0, edges, len(p.w))
+
+    def stale(iq):
+        with pytest.raises(qcx.QcxError) as e:
+            ctx.loss_function(iq, QCX_FP64)
+        assert e.value.status == 7
+
+    ctx.pair_density(0, p.G_int, QCX_FP64)           # new pair densities of q 0
+    stale(0)
+    ctx.loss_function(1, QCX_FP64)                   # q 1 untouched
+    with pytest.raises(qcx.QcxError) as e:
+        ctx.bin_loss([0, 1], 0, edges, len(p.w))
+    assert e.value.status == 7
+    ctx.chi0(0, p.w, p.eta, QCX_FP64)
+    stale(0)
+    ctx.invert_eps(0, QCX_FP64)
+    La, _ = ctx.loss_function(0, QCX_FP64)
+    assert np.allclose(La, L0, rtol=1e-14, atol=0)   # same inputs, same tables
+    ctx.chi0(0, p.w[:3], p.eta, QCX_FP64)            # other frequencies
+    stale(0)
+    ctx.invert_eps(0, QCX_FP64)
+    Lb, _ = ctx.loss_function(0, QCX_FP64)
+    assert Lb.shape == (3, p.G_int.shape[0]) and np.allclose(Lb, L0[:3], rtol=1e-12, atol=0)
+    set_oracle_states(ctx, p, [0, 1], st[0][0], [s[1] for s in st])   # new states: every table resets
+    stale(0)
+    stale(1)
+    with pytest.raises(qcx.QcxError) as e:
+        ctx.pair_density(0, p.G_int[:0], QCX_FP64)   # no G vectors
+    assert e.value.status == 1
+    ctx.pair_density(0, p.G_int, QCX_FP64)
+    with pytest.raises(qcx.QcxError) as e:
+        ctx.chi0(0, np.zeros(0), p.eta, QCX_FP64)    # no frequencies
+    assert e.value.status == 1
