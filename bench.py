@@ -108,6 +108,12 @@ def _barrier_max(ws, value):
     return float(t.item())
 
 
+def _config(ws, precision, blocks_per_step=10000):
+    """The workload both arms report (the reference arm adds its own precision)."""
+    return {"workload": WORKLOAD, "blocks_per_step": blocks_per_step, "l2": "inputs larger than L2 (no flush)",
+            "precision": precision, "parallelism": f"q shards x {ws}"}
+
+
 def _weak_value(nq, nw, steps, ws, ms_max):
     """Whole-job blocks/s: every rank processes its own nq x nw blocks per step;
     the time is the slowest rank's."""
@@ -177,7 +183,8 @@ def run_reference(args, ws, rank):
     out = {"metric": METRIC, "value": v, "unit": "blocks/s", "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 10000 / v / 1.0,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "data": "synthetic",
+           "config": _config(1, "the FP64 oracle (plain numpy, complex128) on a bounded sample of the workload"),
            "cpu_baseline": {"value": v, "unit": "blocks/s", "cores": cpu_cores(), "kind": "oracle", "sample": desc},
            "e2e": {"value": v, "unit": "blocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -343,11 +350,9 @@ def run_ours(args, ws, rank, local):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "bf16",
                "data": "synthetic (seeded states shaped like the paper's workloads)",
-               "config": {"workload": WORKLOAD, "blocks_per_step": nq * nw, "l2": "inputs larger than L2 (no flush)",
-                          "precision": "chi0 BF16 three-term split (6 products) with FP32 accumulation promoted "
-                                       "per K stage and FP64 partial sums; pair densities FP32; inverse FP32 + "
-                                       "FP64 diagonal correction; rate FP64",
-                          "parallelism": f"q shards x {ws}"},
+               "config": _config(ws, "chi0 BF16 three-term split (6 products) with FP32 accumulation promoted "
+                                     "per K stage and FP64 partial sums; pair densities FP32; inverse FP32 + "
+                                     "FP64 diagonal correction; rate FP64", nq * nw),
                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak, "traffic": CHI0_TRAFFIC_BYTES,
                             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_chi0_tc "
