@@ -396,6 +396,27 @@ def test_rate_scalings_and_form_factor_limits():
     assert np.isclose(spec.sum(), np.sum(r1[wev >= ph.w_gap_eV]) * dw, rtol=1e-13)
 
 
+def test_recoil_spectrum_assigns_each_frequency_to_its_ionisation_step():
+    """Eq. (excitation_rate) with the step model Q(w) = 1 + floor((w - w_gap)/w_pp)
+    (0 below the gap): hand-checked values on both sides of each step, and a
+    rate that is nonzero at single frequencies lands in exactly those Q."""
+    gap, pp = 1.1, 3.75
+    for wv, q in ((0.5, 0), (1.0999, 0), (1.1, 1), (4.8499, 1), (4.8501, 2), (8.6001, 3), (12.34, 3), (12.36, 4)):
+        assert rate.ionisation_q(wv, gap, pp) == q, (wv, q)
+    ph = rate.HaloParams()
+    w = np.linspace(0.0, 30.0, 301) / rate.HARTREE_EV        # 0.1 eV steps
+    dR = np.zeros(301)
+    dR[[5, 20, 60, 100, 250]] = [7.0, 1.0, 2.0, 3.0, 4.0]     # 0.5, 2.0, 6.0, 10.0, 25.0 eV
+    spec = rate.recoil_spectrum(w, dR, ph, 8)
+    dw = 0.1
+    want = np.zeros(8)
+    want[0] += 1.0 * dw          # 2.0 eV -> Q = 1
+    want[1] += 2.0 * dw          # 6.0 eV -> Q = 1 + floor(4.9 / 3.75) = 2
+    want[2] += 3.0 * dw          # 10.0 eV -> Q = 1 + floor(8.9 / 3.75) = 3
+    want[6] += 4.0 * dw          # 25.0 eV -> Q = 1 + floor(23.9 / 3.75) = 7
+    assert np.allclose(spec, want, rtol=1e-12, atol=1e-15)   # 0.5 eV is below the gap
+
+
 def test_rate_units_against_an_si_evaluation():
     """The natural-unit rate (eV, hbar = c = 1; Eq. (general_rate) with
     Eq. (dynamic_structure_factor)) against the same formula written in SI
