@@ -88,6 +88,8 @@ typedef struct {
 } qcx_halo_params;
 
 /* ---------------------------------------------------------------- context */
+/* Contexts, streams and error reporting are library plumbing; the paper has
+ * no counterpart. */
 
 /* Create a context on CUDA device `device` using `cuda_stream` (a
  * cudaStream_t; NULL = a new non-blocking stream owned by the context).
@@ -185,7 +187,8 @@ qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, q
 qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out_diag_inv,
                           qcx_c64* out_eps_diag, double* out_resid);
 
-/* Mixed path of qcx_invert_eps: blocks whose condition estimate
+/* A setting of the mixed path of qcx_invert_eps (no counterpart in the
+ * paper; the loss it serves is Eq. (eps_LFE)): blocks whose condition estimate
  * kappa_1 = |eps|_1 |X|_1 (X the FP32 inverse) exceeds kappa1 get the FP64
  * correction of the diagonal (the precision plan's FP64 residual near the
  * plasmon, where eps is ill-conditioned); the others take L_LFE as the
@@ -258,7 +261,8 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
                            const double* inst_gmax, double eta, qcx_precision prec, double* out_L_lfe_head,
                            double* out_L_nolfe_head, int* out_ng);
 
-/* Facts about the current batch plan, written to out[0 .. n-1] (host):
+/* Facts about the current batch plan (batching has no counterpart in the
+ * paper), written to out[0 .. n-1] (host):
  * [0] tile width cap (columns of G per tensor-core tile), [1] tiles,
  * [2] persistent tensor-core CTAs, [3] solve CTAs, [4] kernels per replay,
  * [5] 1 if the tile width was autotuned, [6] distinct q, [7] largest N_G,
@@ -267,7 +271,7 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
 qcx_status qcx_batch_info(const qcx_ctx* ctx, int n, long long* out);
 
 /* Turn the tile-width autotuning of new QCX_MIXED batch plans on (default)
- * or off (then the widest tiles are used).  Errors: QCX_ERR_ARG (ctx NULL). */
+ * or off (then the widest tiles are used); no counterpart in the paper.  Errors: QCX_ERR_ARG (ctx NULL). */
 qcx_status qcx_batch_autotune(qcx_ctx* ctx, int enable);
 
 /* ----------------------------------------- learned local-field correction */
@@ -328,7 +332,7 @@ qcx_status qcx_mlp_predict(qcx_ctx* ctx, int n, const float* X, float* out_mu, f
 
 /* The surrogate route for the heads.  qcx_head_nolfe: L_noLFE at the head
  * of q number iq for nw frequencies (Hartree, host or device), from
- * eps_00 = 1 - v(q) chi0_00 with chi0_00 = 2/(N_k V) sum_t W_t |rho_t(q)|^2
+ * Eq. (eps_noLFE) at G = 0: eps_00 = 1 - v(q) chi0_00 with chi0_00 = 2/(N_k V) sum_t W_t |rho_t(q)|^2
  * in FP64 (only rho at G = 0 is formed).  It uses the context's FP64 per-q
  * state, so a later qcx_chi0 needs qcx_pair_density again.
  * Errors: QCX_ERR_STATE, QCX_ERR_ARG (q = 0 among them), QCX_ERR_ALLOC,
