@@ -21,6 +21,9 @@ Each function follows one step of the method as the paper states it:
   (excitation_rate) in the nonrelativistic halo limit of Appendix A.
 * ``mlp``: the learned local-field correction (no counterpart in the paper):
   network, Gaussian negative log-likelihood, back-propagation and Adam.
+* ``spectral``: the spectral route to chi0 (Eq. (eRPA_spectral) binned on an
+  energy grid once per q, the principal part by the Kramers-Kronig step with
+  the direct sum's broadening); no GPU path yet.
 
 Parity status of every function is listed in the module docstrings; each is
 pinned by a test in ``tests/test_oracle_*.py``.
