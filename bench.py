@@ -30,9 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one k_chi0_tc launch over 1 q x 200 w of the mid workload, from one ncu capture
-# of `bench.py --profile-case mid200` (profiles/k_chi0_tc_traffic_mid_1q200w.md); to be retaken whenever the
-# kernel changes.
-CHI0_TRAFFIC_BYTES = 923490816 + 182294016
+# of `bench.py --profile-case mid200` (dram__bytes_read.sum + dram__bytes_write.sum), and the commit of the kernel
+# source it was taken at; None once the kernel has changed since.
+CHI0_TRAFFIC = None
 METRIC = "eps^-1 (q,w) blocks/s vs FP64 plain GPU path at <=1e-4 rel err; tensor-pipe %"
 WORKLOAD = ("mid: diamond a=5.43 A, 12 sp shells/atom (N_b=96), 8x8x8 k, N_v=4, N_c=32 (N_t=65536), "
             "N_G=181, 50 q x 200 w on 0-60 eV, eta=0.1 eV")
@@ -45,8 +45,20 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
 
 
+def device_uuid(local):
+    """nvidia-smi's id of the CUDA device in use ("GPU-<uuid>"): nvidia-smi
+    ignores CUDA_VISIBLE_DEVICES, so a CUDA ordinal may name another GPU."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms on the GPU
+    given by its UUID (or index when the UUID is unknown)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -88,7 +100,7 @@ class ClockSampler:
                     if r[5 + i].lower().startswith("active"):
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "gpu": str(self.device)}
 
 
 def _dist():
@@ -202,6 +214,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     ctx = qcx.Context(local, stream=stream.cuda_stream)
+    ctx.set_chi0_products(args.products)
     prob = synth.make_mid()
     if ws > 1:   # weak scaling: each rank a different 50-q shard of the same distribution
         prob = synth.make_mid_shard(rank)
@@ -251,7 +264,7 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(device_uuid(local) or local)
     sampler.start()
     _barrier(ws)
     torch.cuda.synchronize()
@@ -312,8 +325,13 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_ms = _barrier_max(ws, e0.elapsed_time(e1) / n_e2e)
 
+    # ------------------------------------ accuracy over every q: mixed vs the FP64 GPU path
+    # The e2e step left the mixed loss tables of all q in the context; each q is then recomputed by the
+    # FP64 path (pinned to the oracle at 1e-10) at eight frequencies.
+    accuracy = accuracy_sweep(ctx, prob, G, w, eta, outL) if not args.no_sweep else None
+
     # -------------------------------------------------- FP64 plain GPU path (sample)
-    nw64 = 8
+    nw64 = 40
     w64 = w[np.linspace(1, nw - 1, nw64).astype(int)]
     ctx.pair_density(0, G, QCX_FP64)
     ctx.chi0(0, w64, eta, QCX_FP64)
@@ -330,6 +348,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     per_block64 = (t[0].elapsed_time(t[1]) / nw + t[1].elapsed_time(t[3]) / nw64) / 1e3
     fp64_value = 1.0 / per_block64
+    chi64_ms = t[1].elapsed_time(t[2])
+    chi64_tflops = 8.0 * nt * ng * ng * nw64 / (chi64_ms / 1e3) / 1e12
+    fma = fma_peaks(local)
 
     # ------------------------------------------- batched uneven instances (rank 0, N=1)
     batched = batched_leg(stream) if (rank == 0 and ws == 1) else None
@@ -350,14 +371,16 @@ def run_ours(args, ws, rank, local):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "bf16",
                "data": "synthetic (seeded states shaped like the paper's workloads)",
-               "config": _config(ws, "chi0 BF16 three-term split (6 products) with FP32 accumulation promoted "
-                                     "per K stage and FP64 partial sums; pair densities FP32; inverse FP32 + "
-                                     "FP64 diagonal correction; rate FP64", nq * nw),
+               "config": _config(ws, f"chi0 as split-BF16 products (two BF16 terms per operand, {args.products} "
+                                     f"products) with FP32 accumulation restarted every 24 MMAs and FP64 partial "
+                                     f"sums; pair densities FP32; inverse FP32 + FP64 diagonal correction; rate "
+                                     f"FP64", nq * nw),
                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": CHI0_TRAFFIC_BYTES,
-                            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_chi0_tc "
-                                              "launch of 1 q x 200 w (the launch this step times), "
-                                              "profiles/k_chi0_tc_traffic_mid_1q200w.md",
+                            "frac": achieved / peak,
+                            "traffic": CHI0_TRAFFIC["bytes"] if CHI0_TRAFFIC else None,
+                            "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_chi0_tc "
+                                               f"launch of 1 q x 200 w at commit {CHI0_TRAFFIC['commit']}"
+                                               if CHI0_TRAFFIC else "not retaken since the kernel changed"),
                             "kernel": "k_chi0_tc", "flops_per_launch": pref_flops,
                             "avg_launch_ms": chi_avg,
                             "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)"},
@@ -365,16 +388,23 @@ def run_ours(args, ws, rank, local):
                                 "algorithmic_bytes": pd_bytes, "achieved_GBs": pd_bytes / (pd_avg / 1e3) / 1e9,
                                 "hbm_peak_GBs": peaks.get("hbm_gbs", 6800.0),
                                 "hbm_frac": pd_bytes / (pd_avg / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                                "note": "FP32 lattice sums of the Gaussian-pair blocks bound it, not HBM "
-                                        "(profiles/k_pair_density_fused_mid_1q.md)"},
+                                "note": "FP32 lattice sums of the Gaussian-pair blocks bound it, not HBM"},
                "e2e": {"value": nq * nw * ws / (e2e_ms / 1e3), "unit": "blocks/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
                "fp64_gpu": {"value": fp64_value, "unit": "blocks/s",
                             "sample": f"1 q: FP64 pair densities amortised over {nw} w + FP64 chi0/inverse "
-                                      f"for {nw64} w"},
+                                      f"for {nw64} w",
+                            "chi0_kernel": "k_chi0_fp64", "chi0_ms": chi64_ms, "chi0_tflops": chi64_tflops,
+                            "fp64_peak_tflops": fma.get("fp64_tflops"),
+                            "chi0_frac_of_fp64_peak": (chi64_tflops / fma["fp64_tflops"]
+                                                       if fma.get("fp64_tflops") else None),
+                            "peak_source": "DFMA microbenchmark measured in this run (libqcx_peaks)"},
+               "fma_peaks": fma,
                "speedup_vs_fp64_gpu": value / fp64_value,
                "gpu_launches": launches_per_step * args.steps,
                "clocks": clocks}
+        if accuracy:
+            out["accuracy"] = accuracy
         if cpu:
             out["cpu_baseline"] = cpu
         if batched:
@@ -383,6 +413,51 @@ def run_ours(args, ws, rank, local):
             out["surrogate"] = surro
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+def fma_peaks(device):
+    """Measured FP64 (DFMA) and FP32 (FFMA) peaks of the CUDA cores."""
+    import ctypes as ct
+    from paper_2603_12326_gb300 import build as b
+    try:
+        lib = ct.CDLL(b.PEAKS_LIB)
+    except OSError:
+        return {}
+    f = lib.qcx_peak_fma
+    f.restype = ct.c_int
+    f.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+    out = {}
+    for name, fp64, iters in (("fp64", 1, 6000), ("fp32", 0, 200000)):
+        tf, ms = ct.c_double(), ct.c_double()
+        if f(device, fp64, 4, iters, 5, ct.byref(tf), ct.byref(ms)) == 0:
+            out[f"{name}_tflops"] = tf.value
+            out[f"{name}_ms"] = ms.value
+    out["method"] = ("8 independent FMA chains per thread, 4 CTAs of 256 threads per SM, best of 5 launches "
+                     "timed with CUDA events")
+    return out
+
+
+def accuracy_sweep(ctx, prob, G, w, eta, outL, nsample=8):
+    """Worst relative error of the mixed loss tables (outL[q][0|1][w][G], all
+    200 w) against the FP64 GPU path at nsample frequencies of every q, per
+    spectrum where L > 1e-3 of its maximum over all frequencies."""
+    from paper_2603_12326_gb300 import QCX_FP64
+    sample = np.linspace(1, len(w) - 1, nsample).astype(int)
+    worst = [0.0, 0.0]
+    for iq in range(prob.nq):
+        ctx.pair_density(iq, G, QCX_FP64)
+        ctx.chi0(iq, w[sample], eta, QCX_FP64)
+        ctx.invert_eps(iq, QCX_FP64, want=False)
+        d = ctx.loss_function(iq, QCX_FP64)
+        for j in range(2):
+            m = outL[iq, j].numpy()
+            top = np.max(np.abs(m), axis=0, keepdims=True)
+            mask = np.abs(d[j]) > 1e-3 * top
+            worst[j] = max(worst[j], float(np.max(np.abs(m[sample][mask] - d[j][mask]) / np.abs(d[j][mask]))))
+    return {"L_lfe_max_rel_err": worst[0], "L_nolfe_max_rel_err": worst[1], "bar": 1e-4,
+            "vs": "FP64 GPU path (held to 1e-10 of the oracle)",
+            "sample": f"all {prob.nq} q x {nsample} w of the timed workload, every G; per spectrum where "
+                      f"L > 1e-3 of its maximum over the {len(w)} w"}
 
 
 def batched_leg(stream, reps=10):
@@ -525,7 +600,7 @@ def run_profile_case_mlp():
     print("profile case done")
 
 
-def run_profile_case(nw=50):
+def run_profile_case(nw=50, products=3):
     """1 q x nw w of the mid workload through the mixed path, twice (nw = 200 is the
     launch configuration the benchmark step times)."""
     import torch
@@ -535,6 +610,7 @@ def run_profile_case(nw=50):
     from paper_2603_12326_gb300.build import build
     build()
     ctx = qcx.Context(0)
+    ctx.set_chi0_products(products)
     prob = synth.make_mid(nq=1, nw=nw)
     states.load_problem(ctx, prob)
     for _ in range(2):
@@ -547,6 +623,17 @@ def run_profile_case(nw=50):
     print("profile case done")
 
 
+def _relaunch(n):
+    """Re-run this command as n ranks (torch.distributed.run, 127.0.0.1)."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    os.execv(sys.executable, cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,11 +642,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-correction leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the accuracy sweep over every q")
+    ap.add_argument("--products", type=int, default=3, choices=[3, 4],
+                    help="split-BF16 products of the mixed chi0 (3: a0b0+a0b1+a1b0, 4: also a1b1)")
     ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "mid200", "batch", "mlp"],
                     help="small case for profilers, no report: mid = 1 q x 50 w of the mid workload, 2 passes; "
                          "batch = the uneven workload once; mlp = one gradient and one prediction")
     args = ap.parse_args()
     ws, rank, local = _dist()
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        # started without a launcher: start the N ranks here, one process per GPU
+        _relaunch(args.gpus)
+    if ws != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but the launcher started {ws} rank(s)")
     if ws > 1:
         import torch
         import torch.distributed as dist
@@ -568,9 +663,9 @@ def main():
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
     if args.profile_case == "mid":
-        run_profile_case()
+        run_profile_case(products=args.products)
     elif args.profile_case == "mid200":
-        run_profile_case(200)
+        run_profile_case(200, products=args.products)
     elif args.profile_case == "batch":
         run_profile_case_batch()
     elif args.profile_case == "mlp":

@@ -58,9 +58,10 @@ typedef enum {
 
 typedef enum {
     QCX_FP64 = 0,   /* plain FP64 throughout                                                    */
-    QCX_MIXED = 1   /* FP32 pair densities kept as three BF16 terms; chi0 as three-term split-BF16
-                       tcgen05 products (the six of order <= 2) with the FP32 tensor-core sums
-                       promoted every two K stages and accumulated in FP64; eps stored in FP64;
+    QCX_MIXED = 1   /* FP32 pair densities kept as two BF16 terms; chi0 as split-BF16 tcgen05
+                       products (three terms a0 b0 + a0 b1 + a1 b0 by default, see
+                       qcx_set_chi0_products) with the FP32 tensor-core sums restarted every
+                       24 MMAs and accumulated in FP64; eps stored in FP64;
                        FP32 Gauss-Jordan inverse with an FP64 residual correction of the diagonal
                        for ill-conditioned blocks (kappa_1 above qcx_set_refine_threshold, 1e4
                        by default) and the other blocks' loss as a quadratic form of the FP64
@@ -150,7 +151,7 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
 /* Pair densities for q number iq and the G set G_int[ng][3]
  * (Eq. (RPA) matrix elements; closed-form Gaussian-product integrals with
  * the lattice sum done as separable one-dimensional sums).  The result is
- * kept in the context (FP64 for QCX_FP64; FP32 values stored as three
+ * kept in the context (FP64 for QCX_FP64; FP32 values stored as two
  * BF16 terms for QCX_MIXED) and, if out_rho != NULL, also written to
  * out_rho[nt][ng] (complex double).  Starts a new q: the context's chi0,
  * eps and loss tables for other q are untouched; those for iq are reset.
@@ -197,6 +198,31 @@ qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out
  * of this context.  Errors: QCX_ERR_ARG (ctx NULL, kappa1 negative or NaN). */
 qcx_status qcx_set_refine_threshold(qcx_ctx* ctx, double kappa1);
 
+/* Precision setting of the mixed chi0 (the split-BF16 products of Eq. (RPA)'s
+ * contraction; the product count is not the paper's, which works in FP64):
+ * nprod = 3 accumulates a0 b0 + a0 b1 + a1 b0 of the two-term BF16 splits
+ * a = a0 + a1, b = b0 + b1 (the default), nprod = 4 adds a1 b1.  Applies to
+ * later qcx_chi0 calls and to batch plans built afterwards.
+ * Errors: QCX_ERR_ARG (ctx NULL, nprod not 3 or 4). */
+qcx_status qcx_set_chi0_products(qcx_ctx* ctx, int nprod);
+
+/* Failure handling, no counterpart in the paper: every wait inside the
+ * tensor-core chi0 kernels (qcx_chi0 with QCX_MIXED, and the batch plans of
+ * qcx_solve_batch built after this call) gives up after `cycles` SM clock
+ * cycles (default 4e9, about 2 s); the kernel then stops its pipeline, lets its
+ * own copies and MMAs finish, frees its tensor memory and returns, and the
+ * call reports QCX_ERR_TIMEOUT with invalid results while the context stays
+ * usable.  A short limit makes the waits run out on purpose (tests).
+ * Errors: QCX_ERR_ARG (ctx NULL, cycles < 1). */
+qcx_status qcx_set_wait_limit(qcx_ctx* ctx, long long cycles);
+
+/* Fault injection for tests of the failure path (no counterpart in the
+ * paper): with withhold_copies != 0 the tensor-core kernel of qcx_chi0
+ * (QCX_MIXED) issues none of its copies, so its consumers' waits run out after
+ * the limit of qcx_set_wait_limit and the call returns QCX_ERR_TIMEOUT; 0
+ * (the default) restores normal operation.  Errors: QCX_ERR_ARG (ctx NULL). */
+qcx_status qcx_set_fault_injection(qcx_ctx* ctx, int withhold_copies);
+
 /* Loss functions of q number iq (Eq. (dynamic_structure_factor)):
  *   out_L_lfe[nw][ng]   = -Im [eps^-1]_GG   (with local fields)
  *   out_L_nolfe[nw][ng] = -Im (1/eps_GG)    (without)
@@ -236,8 +262,8 @@ qcx_status qcx_rate(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const d
  *   out_L_nolfe_head[i] = -Im (1 / eps_00)
  *   out_ng[i]           = N_G of the instance (may be NULL).
  * eta (Hartree) is shared.  QCX_FP64 computes everything in FP64; QCX_MIXED
- * forms chi0 on the tensor cores (three-term BF16 split, FP32 accumulation
- * promoted to FP64, eps in FP64), factors eps in FP32 (LU, partial pivoting)
+ * forms chi0 on the tensor cores (split-BF16 products as for qcx_chi0, FP32
+ * accumulation promoted to FP64, eps in FP64), factors eps in FP32 (LU, partial pivoting)
  * and refines the head with two FP64-residual correction steps.
  * The first call with a new instance list (same q indices, cutoffs, eta and
  * precision) plans the batch: G sets, pair densities once per distinct q on
@@ -391,12 +417,16 @@ qcx_status qcx_surrogate_heads(qcx_ctx* ctx, int nsel, const int* iq_list, int n
  *   out_singular[nb]        device or NULL: 1 where a zero pivot was met
  *                           (that matrix's outputs are then zero), else 0
  *   cuda_stream             stream to run on (NULL = legacy default stream)
- * The only scratch is a fixed 16 MiB device array inside the library, which
- * every GPU that loads the library holds until the process exits: calls need
- * nb * n * n * 16 bytes <= 16 MiB, otherwise QCX_ERR_ARG and nothing runs.
- * The first call on a device resolves the array's address for that device
- * (cudaGetSymbolAddress with the device current); make that first call before
- * any stream capture.  Every call shares the array and leaves its last
+ * The only scratch is a fixed 16 MiB device array inside the library: calls
+ * need nb * n * n * 16 bytes <= 16 MiB, otherwise QCX_ERR_ARG and nothing
+ * runs.  A device reserves the array when it loads the code of this entry
+ * point; under CUDA's default lazy module loading (CUDA_MODULE_LOADING=LAZY)
+ * that is this entry point's first call on the device, which also resolves
+ * the array's address for that device (cudaGetSymbolAddress with the device
+ * current).  The array is then held until the process exits.  So make the
+ * first call on each device before reserving the rest of the memory budget,
+ * and outside any stream capture; that call can fail with QCX_ERR_CUDA when
+ * the device has no 16 MiB left.  Every call shares the array and leaves its last
  * contents there; every element a call uses is written by that call first,
  * so nothing needs clearing.  Calls that overlap on the GPU (on different
  * streams, or from different threads) race on the array: serialise them.

@@ -17,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqcx.so")
+PEAKS_SRC = os.path.join(HERE, "peaks", "fma_peak.cu")
+PEAKS_LIB = os.path.join(OUT, "libqcx_peaks.so")   # measurement utility (CUDA-core FMA peaks), not the path
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + SRC]
@@ -34,7 +36,9 @@ def sources():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
+        return False
+    if os.path.getmtime(PEAKS_SRC) > os.path.getmtime(PEAKS_LIB):
         return False
     t = os.path.getmtime(LIB)
     deps = sources() + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))]
@@ -58,8 +62,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
+    def peaks():
+        r = subprocess.run([nvcc, *ARCH, *FLAGS, "-shared", PEAKS_SRC, "-o", PEAKS_LIB + ".tmp"], capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(PEAKS_LIB + ".tmp", PEAKS_LIB)
+
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        fut = ex.submit(peaks)
         objs = list(ex.map(one, sources()))
+        fut.result()
     tmp = LIB + ".tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:

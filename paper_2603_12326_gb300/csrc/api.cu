@@ -18,7 +18,7 @@ __global__ void k_to_float(const double* in, float* out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
 }
-// rho [ng][nt] (FP64) or the three BF16 planes [ngp][kp] -> [nt][ng] double2
+// rho [ng][nt] (FP64) or the two BF16 planes [ngp][kp] -> [nt][ng] double2
 __global__ void k_rho_export(int ng, long long nt, const double2* R64, const __nv_bfloat162* p0,
                              long long plane2, long long kp2, double2* out) {
     const long long n = nt * ng;
@@ -32,8 +32,7 @@ __global__ void k_rho_export(int ng, long long nt, const double2* R64, const __n
             const long long o = (long long)g * kp2 + t;
             const float2 a = __bfloat1622float2(p0[o]);
             const float2 b = __bfloat1622float2(p0[o + plane2]);
-            const float2 c = __bfloat1622float2(p0[o + 2 * plane2]);
-            out[i] = make_double2((double)a.x + (double)b.x + (double)c.x, (double)a.y + (double)b.y + (double)c.y);
+            out[i] = make_double2((double)a.x + (double)b.x, (double)a.y + (double)b.y);
         }
     }
 }
@@ -133,6 +132,13 @@ qcx_status qcx_create(qcx_ctx** out, int device, void* cuda_stream) {
         cudaGetLastError();
         delete ctx;
         return QCX_ERR_CUDA;     // kernels are built for sm_103a only
+    }
+    // the kernels of this library must have been built for this device's architecture (10.3)
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void*)k_kmag) != cudaSuccess || fa.binaryVersion != 103) {
+        cudaGetLastError();
+        delete ctx;
+        return QCX_ERR_CUDA;
     }
     ctx->device = device;
     if (cuda_stream) {
@@ -313,7 +319,7 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
     if (prec == QCX_FP64) {
         CUDA_OR_FAIL(s.rho.ensure((size_t)ng * nt * sizeof(double2)), "alloc rho");
     } else {
-        const size_t bytes = 3 * (size_t)s.ngp * s.kp * sizeof(__nv_bfloat16);
+        const size_t bytes = 2 * (size_t)s.ngp * s.kp * sizeof(__nv_bfloat16);
         CUDA_OR_FAIL(s.rho.ensure(bytes), "alloc rho");
         CUDA_OR_FAIL(cudaMemsetAsync(s.rho.p, 0, bytes, ctx->stream), "clear rho");
     }
@@ -429,6 +435,29 @@ qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out
     int bad = 0;
     for (int f : flags) bad += f != 0;
     if (bad) return ctx->fail(QCX_ERR_SINGULAR, "invert: " + std::to_string(bad) + " singular block(s)");
+    return QCX_OK;
+}
+
+qcx_status qcx_set_wait_limit(qcx_ctx* ctx, long long cycles) {
+    if (!ctx) return QCX_ERR_ARG;
+    ctx->err.clear();
+    if (cycles < 1) return ctx->fail(QCX_ERR_ARG, "set_wait_limit: cycles must be positive");
+    ctx->wait_limit = cycles;
+    return QCX_OK;
+}
+
+qcx_status qcx_set_chi0_products(qcx_ctx* ctx, int nprod) {
+    if (!ctx) return QCX_ERR_ARG;
+    ctx->err.clear();
+    if (nprod != 3 && nprod != 4) return ctx->fail(QCX_ERR_ARG, "set_chi0_products: 3 or 4");
+    ctx->chi0_products = nprod;
+    return QCX_OK;
+}
+
+qcx_status qcx_set_fault_injection(qcx_ctx* ctx, int withhold_copies) {
+    if (!ctx) return QCX_ERR_ARG;
+    ctx->err.clear();
+    ctx->withhold_copies = withhold_copies ? 1 : 0;
     return QCX_OK;
 }
 

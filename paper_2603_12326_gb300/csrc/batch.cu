@@ -188,13 +188,15 @@ struct BatchPlan {
 
     DevBuf d_G, d_inst, d_wtab, d_eps, d_work, d_rowmap, d_x, d_r, d_out, d_flags, d_status, d_acc;
     DevBuf d_tiles, d_cta, d_rtask;
-    std::vector<CUtensorMap> maps;              // [nslot][3]
+    std::vector<CUtensorMap> maps;              // [nslot][2]: the two BF16 planes of each slot
     std::vector<int> grp_tile0, grp_ntile;      // tensor-core tiles per group of <= QCX_BATCH_MAXQ slots
     int tc_grid = 0, tile_cap = 0, ntile = 0;
     int lu_grid = 0, n_rtask = 0;
     int tuned = 0;
     double tune_ms = 0.0;
     int launches = 0;
+    int nprod = 3;                              // split-BF16 products of the tensor-core chi0
+    long long wait_limit = 0;                   // pipeline wait limit captured into the graph
     cudaGraphExec_t exec = nullptr;
 
     ~BatchPlan() {
@@ -318,10 +320,11 @@ cudaError_t record(qcx_ctx* ctx, BatchPlan& p) {
             const int s0 = (int)g * QCX_BATCH_MAXQ;
             const int ns = std::min(QCX_BATCH_MAXQ, p.nslot - s0);
             // slot indices inside a group are relative to its first slot
-            e = qcx_launch_chi0_tc_batch(st, p.maps.data() + 3 * s0, s0, ns, p.grp_ntile[g],
+            e = qcx_launch_chi0_tc_batch(st, p.maps.data() + 2 * s0, s0, ns, p.grp_ntile[g],
                                          p.d_tiles.as<int4>() + p.grp_tile0[g], std::min(p.tc_grid, p.grp_ntile[g]),
                                          dinst, p.d_wtab.as<float2>(), p.kp / 2, (int)(p.kp / TC_KSTEP), p.pref,
-                                         p.d_acc.as<double>(), p.d_eps.as<double2>(), p.d_status.as<int>());
+                                         p.d_acc.as<double>(), p.d_eps.as<double2>(), p.d_status.as<int>(),
+                                         p.wait_limit, p.nprod);
             if (e != cudaSuccess) return e;
             ++p.launches;
         }
@@ -456,7 +459,7 @@ qcx_status build_plan(qcx_ctx* ctx, BatchPlan& p) {
         CUDA_OR_FAIL(q->vs.ensure(sizeof(double) * U), "alloc");
         CUDA_OR_FAIL(q->vs32.ensure(sizeof(float) * U), "alloc");
         if (mixed) {
-            const size_t bytes = 3 * (size_t)q->ngp * q->kp * sizeof(__nv_bfloat16);
+            const size_t bytes = 2 * (size_t)q->ngp * q->kp * sizeof(__nv_bfloat16);
             CUDA_OR_FAIL(q->rho.ensure(bytes), "alloc rho");
             CUDA_OR_FAIL(cudaMemsetAsync(q->rho.p, 0, bytes, ctx->stream), "clear rho");
         } else {
@@ -525,13 +528,13 @@ qcx_status build_plan(qcx_ctx* ctx, BatchPlan& p) {
     }
     if (mixed) {
         CUDA_OR_FAIL(p.d_wtab.ensure(sizeof(float2) * (size_t)ninst * (p.kp / 2)), "alloc W");
-        p.maps.resize(3 * p.nslot);
+        p.maps.resize(2 * p.nslot);
         for (int s = 0; s < p.nslot; ++s) {
             QSlot& q = *p.qs[s];
             unsigned char* base = reinterpret_cast<unsigned char*>(q.rho.p);
             const size_t plane = (size_t)q.ngp * q.kp * 2;
-            for (int pc = 0; pc < 3; ++pc)
-                if (!qcx_make_bf16_map(&p.maps[3 * s + pc], base + pc * plane, q.kp, q.ngp, 64))
+            for (int pc = 0; pc < 2; ++pc)
+                if (!qcx_make_bf16_map(&p.maps[2 * s + pc], base + pc * plane, q.kp, q.ngp, 64))
                     return ctx->fail(QCX_ERR_CUDA, "solve_batch: tensor map");
         }
     } else {
@@ -684,7 +687,8 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
     }
     BatchPlan* p = ctx->batch;
     const bool same = p && p->gen == ctx->gen && p->prec == (int)prec && p->eta == eta && p->ninst == ninst &&
-                      p->key_q == iq && p->key_gmax == gm;
+                      p->key_q == iq && p->key_gmax == gm && p->nprod == ctx->chi0_products &&
+                      p->wait_limit == ctx->wait_limit;
     if (!same) {
         delete ctx->batch;
         ctx->batch = nullptr;
@@ -696,6 +700,8 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
         p->ninst = ninst;
         p->key_q = iq;
         p->key_gmax = gm;
+        p->nprod = ctx->chi0_products;
+        p->wait_limit = ctx->wait_limit;
         qcx_status st = build_plan(ctx, *p);
         if (st == QCX_OK) st = upload_inst(ctx, *p, w);
         if (st == QCX_OK) st = prepare(ctx, *p);

@@ -5,10 +5,10 @@
 // The arithmetic per tile is that of the per-q kernel: one 64-row G' block
 // of one instance at its frequency (a 128 x N accumulator: 64 re rows and 64
 // im rows of chi0_GG'), one N chunk of its G list, the contraction over
-// k' = 2t + p split into three BF16 terms with the six products of order <= 2,
-// FP32 accumulation restarted every PROMOTE stages and promoted through FP32
-// registers into an FP64 buffer, and eps = delta - v^1/2 chi0 v^1/2 written in
-// FP64 (row G', column G).
+// k' = 2t + p with both operands split into two BF16 terms and the three (or
+// four) split products, FP32 accumulation restarted after 24 MMAs and promoted
+// through FP32 registers into an FP64 buffer, and eps = delta - v^1/2 chi0 v^1/2
+// written in FP64 (row G', column G).
 //
 // What changes is the scheduling (and, as in the per-q kernel, two MMA issuer
 // warps take alternate accumulation windows).  One CTA per SM runs for the whole batch
@@ -30,12 +30,10 @@ namespace {
 
 constexpr int NTHREADS = 384;             // warps: 0 TMA, 1 and 10 MMA, 2-9 A/drain/epilogue, 11 idle
 constexpr int MMA_WARP2 = 10;
-constexpr int NSTAGE = 3;
-constexpr int NPIECE = 3;
+constexpr int NSTAGE = 4;
+constexpr int NPIECE = 2;
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per tile, rows per TMA box
-constexpr int PROMOTE = 2;
-constexpr int FLUSH = 128;
 constexpr int MAXHALF = 96;
 constexpr int NMAX = 2 * MAXHALF;         // largest N of a tile
 constexpr int BREG = NMAX * ROWB;         // one B piece region
@@ -46,7 +44,7 @@ constexpr uint32_t ACC_OFF = 256;         // second TMEM buffer
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_LIMIT = 232448;
 constexpr size_t SMEM_BYTES =
-    1024 + NSTAGE * (size_t)STAGE_BYTES + NSTAGE * TPS * sizeof(float2) + (3 * NSTAGE + 5) * sizeof(uint64_t) + 16;
+    1024 + NSTAGE * (size_t)STAGE_BYTES + NSTAGE * TPS * sizeof(float2) + (5 * NSTAGE + 5) * sizeof(uint64_t) + 16;
 static_assert(SMEM_BYTES <= (size_t)SMEM_LIMIT, "stage ring does not fit in shared memory");
 
 struct MapSet {
@@ -64,6 +62,10 @@ struct BArgs {
     double* acc64;            // [grid][128][NMAX]
     double2* eps;
     int* status;
+    long long wait_limit;     // clock cycles before a pipeline wait gives up
+    int nprod;                // 3: a0b0 + a0b1 + a1b0; 4: also a1b1
+    int promote;              // K stages per accumulation window (24 MMAs)
+    int flush;                // K stages between FP64 flushes (64 windows)
 };
 
 __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_constant__ MapSet maps, BArgs a) {
@@ -73,10 +75,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
     unsigned char* tail = base + NSTAGE * STAGE_BYTES;
     float2* Wbuf = reinterpret_cast<float2*>(tail);
     uint64_t* bars = reinterpret_cast<uint64_t*>(tail + NSTAGE * TPS * sizeof(float2));
-    uint64_t* full_b = bars;
-    uint64_t* full_a = bars + NSTAGE;
-    uint64_t* empty = bars + 2 * NSTAGE;
-    uint64_t* acc_full = bars + 3 * NSTAGE;
+    // copy and A-tile barriers of running stage gs: number gs mod 2 NSTAGE (ring slot gs mod NSTAGE),
+    // so an issuer's wait never meets the previous phase of its barrier unfinished
+    uint64_t* full_b = bars;                   // [2 NSTAGE]
+    uint64_t* full_a = bars + 2 * NSTAGE;      // [2 NSTAGE]
+    uint64_t* empty = bars + 4 * NSTAGE;       // [NSTAGE]
+    uint64_t* acc_full = bars + 5 * NSTAGE;
     uint64_t* drained = acc_full + 2;
     uint64_t* mma_done = drained + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
@@ -86,6 +90,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(&full_b[s], 1);
             mbar_init(&full_a[s], 8);
+            mbar_init(&full_b[s + NSTAGE], 1);
+            mbar_init(&full_a[s + NSTAGE], 8);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -101,7 +107,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
+    const int nwin = (a.kstages + a.promote - 1) / a.promote;
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
@@ -120,27 +126,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                 for (int it = 0; it < a.kstages; ++it, ++gs) {
                     const int s = (int)(gs % NSTAGE);
                     const uint32_t ph = (uint32_t)(gs / NSTAGE) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status, a.wait_limit)) {
                         ok = false;
                         break;
                     }
                     unsigned char* st = base + s * STAGE_BYTES;
-                    mbar_arrive_tx(&full_b[s], bytes);
-                    bulk_load(Wbuf + s * TPS, wrow + (size_t)it * TPS, TPS * sizeof(float2), &full_b[s]);
+                    uint64_t* fb = &full_b[gs % (2 * NSTAGE)];
+                    mbar_arrive_tx(fb, bytes);
+                    bulk_load(Wbuf + s * TPS, wrow + (size_t)it * TPS, TPS * sizeof(float2), fb);
                     for (int p = 0; p < NPIECE; ++p)
                         for (int r = 0; r < nbox; ++r)
-                            tma_load_2d(st + p * BREG + r * SPIECE, &maps.m[slot][p], &full_b[s], it * KSTEP,
+                            tma_load_2d(st + p * BREG + r * SPIECE, &maps.m[slot][p], fb, it * KSTEP,
                                         tl.z + r * GBLK);
                     if (!src_b) {
                         unsigned char* sp = st + NPIECE * BREG;
                         for (int p = 0; p < NPIECE; ++p)
-                            tma_load_2d(sp + p * SPIECE, &maps.m[slot][p], &full_b[s], it * KSTEP, tl.y * GBLK);
+                            tma_load_2d(sp + p * SPIECE, &maps.m[slot][p], fb, it * KSTEP, tl.y * GBLK);
                     }
                     last = gs;
                 }
             }
-            if (last >= 0)
-                mbar_wait(&full_b[last % NSTAGE], (uint32_t)(last / NSTAGE) & 1u, abort_flag, a.status, false);
+            // let every copy still in flight (at most the last NSTAGE stages) land before the CTA can exit
+            for (int gs2 = max(0, last - NSTAGE + 1); gs2 <= last; ++gs2)
+                mbar_wait(&full_b[gs2 % (2 * NSTAGE)], (uint32_t)(gs2 / (2 * NSTAGE)) & 1u, abort_flag, a.status,
+                          CLEANUP_WAIT_LIMIT, false);
         }
     } else if (warp == 1 || warp == MMA_WARP2) {
         // ---------------------------------------------------------- MMA issuers
@@ -156,27 +165,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                     const int gw = lt * nwin + wd;
                     if ((gw & 1) != par) continue;
                     const int b = gw & 1;
-                    if (gw >= 2 && !mbar_wait(&drained[b], (uint32_t)((gw - 2) >> 1) & 1u, abort_flag, a.status)) {
+                    if (gw >= 2 && !mbar_wait(&drained[b], (uint32_t)((gw - 2) >> 1) & 1u, abort_flag, a.status, a.wait_limit)) {
                         ok = false;
                         break;
                     }
-                    const int it1 = min((wd + 1) * PROMOTE, a.kstages);
-                    for (int it = wd * PROMOTE; it < it1; ++it) {
+                    const int it1 = min((wd + 1) * a.promote, a.kstages);
+                    for (int it = wd * a.promote; it < it1; ++it) {
                         const int gs = lt * a.kstages + it;
                         const int s = gs % NSTAGE;
-                        const uint32_t ph = (uint32_t)(gs / NSTAGE) & 1u;
-                        const bool first = it == wd * PROMOTE;
+                        const bool first = it == wd * a.promote;
                         // the A warps arrive only after they saw this stage's copies land
-                        if (!mbar_wait(&full_a[s], ph, abort_flag, a.status)) {
+                        if (!mbar_wait(&full_a[gs % (2 * NSTAGE)], (uint32_t)(gs / (2 * NSTAGE)) & 1u, abort_flag,
+                                       a.status, a.wait_limit)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                         unsigned char* st = base + s * STAGE_BYTES;
-                        const uint32_t b0 = smem_u32(st), b1 = b0 + BREG, b2 = b1 + BREG;
+                        const uint32_t b0 = smem_u32(st), b1 = b0 + BREG;
                         const uint32_t d = tmem + (uint32_t)b * ACC_OFF;
-                        const uint32_t a0 = smem_u32(st + NPIECE * BREG + NPIECE * SPIECE), a1 = a0 + ATILE,
-                                       a2 = a1 + ATILE;
+                        const uint32_t a0 = smem_u32(st + NPIECE * BREG + NPIECE * SPIECE), a1 = a0 + ATILE;
 #pragma unroll
                         for (int kk = 0; kk < KSTEP / 16; ++kk) {
                             const uint32_t off = kk * 32;
@@ -184,9 +192,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                                       (first && kk == 0) ? 0u : 1u);
                             umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
                             umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
-                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
-                            umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                            if (a.nprod == 4) umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
                         }
                         umma_commit(&empty[s]);
                     }
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
             }
             // no MMA of either issuer may still be running when TMEM is freed
             umma_commit(mma_done);
-            mbar_wait(mma_done, 0, abort_flag, a.status, false);
+            mbar_wait(mma_done, 0, abort_flag, a.status, CLEANUP_WAIT_LIMIT, false);
         }
     } else if (warp < MMA_WARP2) {
         // ------------------------- A generation, accumulator drain, epilogue
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
             auto drain = [&](int wd) -> bool {
                 const int gw = lt * nwin + wd;
                 const int b = gw & 1;
-                if (!warp_wait(&acc_full[b], (uint32_t)(gw >> 1) & 1u, abort_flag, a.status)) return false;
+                if (!warp_wait(&acc_full[b], (uint32_t)(gw >> 1) & 1u, abort_flag, a.status, a.wait_limit)) return false;
                 tc_fence_after();
                 const uint32_t tb = tmem + lane_off + (uint32_t)b * ACC_OFF + (uint32_t)(hc * nch8 * 8);
 #pragma unroll
@@ -247,9 +253,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&drained[b]);
-                if (((wd + 1) * PROMOTE) % FLUSH == 0 || wd + 1 == nwin) {
+                if (((wd + 1) * a.promote) % a.flush == 0 || wd + 1 == nwin) {
                     // the first flush of a tile starts the FP64 sums
-                    const bool flushed = wd >= FLUSH / PROMOTE;
+                    const bool flushed = wd >= a.flush / a.promote;
                     double* acc64 = a.acc64 + ((size_t)blockIdx.x * 128 + row) * NMAX + hc * nch8 * 8;
 #pragma unroll
                     for (int c = 0; c < MAXHALF; ++c) {
@@ -265,57 +271,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
             for (int it = 0; it < a.kstages; ++it) {
                 const int gs = lt * a.kstages + it;
                 const int s = gs % NSTAGE;
-                const uint32_t ph = (uint32_t)(gs / NSTAGE) & 1u;
+                const int s2 = gs % (2 * NSTAGE);
                 // the producer issued this stage's copies only after the MMAs of its previous
                 // use finished, so a landed stage is also free to overwrite
-                if (!(ok = warp_wait(&full_b[s], ph, abort_flag, a.status))) break;
+                if (!(ok = warp_wait(&full_b[s2], (uint32_t)(gs / (2 * NSTAGE)) & 1u, abort_flag, a.status,
+                                     a.wait_limit)))
+                    break;
                 unsigned char* st = base + s * STAGE_BYTES;
                 const unsigned char* srcb = st + (src_b ? 0 : NPIECE * BREG);
                 const uint32_t src_piece = src_b ? (uint32_t)BREG : (uint32_t)SPIECE;
-                uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};
-                uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0}, im2[4] = {0, 0, 0, 0};
+                uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0};
+                uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0};
                 if (go < lim) {
                     const uint32_t coff = sw64_off(row0 + go, j);
                     const uint4 h0 = *reinterpret_cast<const uint4*>(srcb + coff);
                     const uint4 h1 = *reinterpret_cast<const uint4*>(srcb + src_piece + coff);
-                    const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
-                    const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
-                                   v2[4] = {h2.x, h2.y, h2.z, h2.w};
+                    const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w};
                     const float4* Wv4 = reinterpret_cast<const float4*>(Wbuf + s * TPS + 4 * j);
                     const float4 wa = Wv4[0], wb = Wv4[1];
                     const float2 Wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
                                           make_float2(wb.z, wb.w)};
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
-                        const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
-                        const float rr = f0.x + (f1.x + f2.x), ri = f0.y + (f1.y + f2.y);
+                        const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]);
+                        const float rr = f0.x + f1.x, ri = f0.y + f1.y;
                         const float2 wq = Wv[qq];
                         const float xr = wq.x * rr - wq.y * ri;
                         const float xi = wq.x * ri + wq.y * rr;
-                        split3(xr, xi, re0[qq], re1[qq], re2[qq]);
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(xr, xi);
+                        const float2 hf = __bfloat1622float2(h);
+                        re0[qq] = *reinterpret_cast<const uint32_t*>(&h);
+                        re1[qq] = pack_bf16(xr - hf.x, xi - hf.y);
                         // (xi, -xr) splits into the terms of (xr, xi), swapped, the second negated
                         im0[qq] = __byte_perm(re0[qq], 0u, 0x1032) ^ 0x80000000u;
                         im1[qq] = __byte_perm(re1[qq], 0u, 0x1032) ^ 0x80000000u;
-                        im2[qq] = __byte_perm(re2[qq], 0u, 0x1032) ^ 0x80000000u;
                     }
                 }
                 unsigned char* ap = st + NPIECE * BREG + NPIECE * SPIECE;
                 const uint32_t o_re = sw64_off(go, j), o_im = sw64_off(64 + go, j);
                 *reinterpret_cast<uint4*>(ap + o_re) = make_uint4(re0[0], re0[1], re0[2], re0[3]);
                 *reinterpret_cast<uint4*>(ap + ATILE + o_re) = make_uint4(re1[0], re1[1], re1[2], re1[3]);
-                *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_re) = make_uint4(re2[0], re2[1], re2[2], re2[3]);
                 *reinterpret_cast<uint4*>(ap + o_im) = make_uint4(im0[0], im0[1], im0[2], im0[3]);
                 *reinterpret_cast<uint4*>(ap + ATILE + o_im) = make_uint4(im1[0], im1[1], im1[2], im1[3]);
-                *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_im) = make_uint4(im2[0], im2[1], im2[2], im2[3]);
                 fence_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&full_a[s]);
+                if (lane == 0) mbar_arrive(&full_a[s2]);
                 // drain the previous window once this window's A tiles are queued; after the
                 // last stage drain whatever is left (one call site keeps the code compact)
                 int wd0 = nwin, wd1 = -1;
-                if (it % PROMOTE == PROMOTE - 1 && it >= PROMOTE) wd0 = wd1 = it / PROMOTE - 1;
+                if (it % a.promote == a.promote - 1 && it >= a.promote) wd0 = wd1 = it / a.promote - 1;
                 if (it + 1 == a.kstages) {
-                    wd0 = min(wd0, (it % PROMOTE == PROMOTE - 1 && it >= PROMOTE) ? it / PROMOTE - 1 : max(nwin - 2, 0));
+                    wd0 = min(wd0, (it % a.promote == a.promote - 1 && it >= a.promote) ? it / a.promote - 1
+                                                                                        : max(nwin - 2, 0));
                     wd1 = nwin - 1;
                 }
                 for (int wd = wd0; wd <= wd1 && ok; ++wd) ok = drain(wd);
@@ -357,12 +364,13 @@ size_t qcx_chi0_tc_batch_acc_bytes(int grid) { return (size_t)grid * 128 * NMAX 
 cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, int slot0, int nslot, int ntile,
                                      const int4* d_tiles, int grid, const BatchInst* d_inst, const float2* wtab,
                                      long long wld, int kstages, double pref, double* acc64, double2* eps,
-                                     int* status) {
-    if (nslot < 1 || nslot > QCX_BATCH_MAXQ || ntile < 1 || grid < 1 || kstages < 1) return cudaErrorInvalidValue;
+                                     int* status, long long wait_limit, int nprod) {
+    if (nslot < 1 || nslot > QCX_BATCH_MAXQ || ntile < 1 || grid < 1 || kstages < 1 || (nprod != 3 && nprod != 4))
+        return cudaErrorInvalidValue;
     MapSet ms;
     memset(&ms, 0, sizeof(ms));
     for (int s = 0; s < nslot; ++s)
-        for (int p = 0; p < NPIECE; ++p) ms.m[s][p] = maps[3 * s + p];
+        for (int p = 0; p < NPIECE; ++p) ms.m[s][p] = maps[NPIECE * s + p];
     BArgs a;
     a.ntile = ntile;
     a.kstages = kstages;
@@ -375,6 +383,10 @@ cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, i
     a.acc64 = acc64;
     a.eps = eps;
     a.status = status;
+    a.wait_limit = wait_limit;
+    a.nprod = nprod;
+    a.promote = 24 / ((KSTEP / 16) * nprod);
+    a.flush = 64 * a.promote;
     cudaError_t e =
         cudaFuncSetAttribute((const void*)k_chi0_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;

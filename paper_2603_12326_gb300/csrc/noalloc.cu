@@ -7,8 +7,9 @@
 // that reserved its whole memory budget at start-up.  qcx_eps_inverse_diag_noalloc
 // serves them: the caller passes device inputs and outputs, and the only
 // scratch (the per-matrix work copies of the Gauss-Jordan elimination) lives in
-// a file-scope device array of fixed size that every GPU loading the library
-// keeps until the process exits.
+// a file-scope device array of fixed size.  A device reserves it when it loads
+// this file's code (with CUDA's lazy module loading: at the entry point's first
+// call there) and keeps it until the process exits.
 #include "qcx_internal.h"
 #include "cplx.cuh"
 
@@ -125,9 +126,12 @@ __global__ void __launch_bounds__(NA_THREADS)
     }
     if (s_bad) {
         if (threadIdx.x == 0 && flags) flags[b] = 1;
+        // every output of a singular matrix is zero (its diagonal may itself be zero, so the
+        // no-LFE values written above are replaced as well)
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             diag_inv[(size_t)b * n + j] = make_double2(0.0, 0.0);
             if (L_lfe) L_lfe[(size_t)b * n + j] = 0.0;
+            if (L_nolfe) L_nolfe[(size_t)b * n + j] = 0.0;
         }
         return;
     }

@@ -50,9 +50,8 @@ template <typename T> struct PDArgs {
     const cplx<T>* Ck;       // [nk][nb][nv]
     const cplx<T>* Ckq;      // [nk][nb][nc]
     double2* R64;            // FP64 output [ng][nt]
-    __nv_bfloat162* R0;      // MIXED output: three BF16 planes [ngp][kp/2] (pairs re, im),
-    __nv_bfloat162* R1;      // x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0),
-    __nv_bfloat162* R2;      // x2 = bf16(x - x0 - x1)
+    __nv_bfloat162* R0;      // MIXED output: two BF16 planes [ngp][kp/2] (pairs re, im),
+    __nv_bfloat162* R1;      // x = x0 + x1 with x0 = bf16(x), x1 = bf16(x - x0)
     long long kp2;           // row length of the bf16 planes in bf16x2 units
     cplx<T>* Sout;           // overlap mode: [nk][nb][nb]
 };
@@ -167,11 +166,14 @@ __device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T k
         }
 }
 
-__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
-    p0 = __float2bfloat16_rn(x);
-    const float r = x - __bfloat162float(p0);
-    p1 = __float2bfloat16_rn(r);
-    p2 = __float2bfloat16_rn(r - __bfloat162float(p1));
+// (re, im) of one FP32 value -> the two BF16 terms of each part, x = x0 + x1 with
+// x0 = bf16(x) and x1 = bf16(x - x0) (round to nearest), written to the two planes
+__device__ __forceinline__ void store_split2(float re, float im, __nv_bfloat162* R0, __nv_bfloat162* R1,
+                                             long long o) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    const float2 hf = __bfloat1622float2(h);
+    R0[o] = h;
+    R1[o] = __floats2bfloat162_rn(re - hf.x, im - hf.y);
 }
 
 template <typename T, int NCH>
@@ -218,13 +220,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
             if (a.R64) {
                 a.R64[(long long)g * a.nt + t] = make_double2((double)acc.x, (double)acc.y);
             } else {
-                __nv_bfloat16 r0, r1, r2, i0, i1, i2;
-                split3_bf16((float)acc.x, r0, r1, r2);
-                split3_bf16((float)acc.y, i0, i1, i2);
-                const long long o = (long long)g * a.kp2 + t;
-                a.R0[o] = __halves2bfloat162(r0, i0);
-                a.R1[o] = __halves2bfloat162(r1, i1);
-                a.R2[o] = __halves2bfloat162(r2, i2);
+                store_split2((float)acc.x, (float)acc.y, a.R0, a.R1, (long long)g * a.kp2 + t);
             }
         }
     }
@@ -303,14 +299,8 @@ __global__ void __launch_bounds__(pdf_maxt<NV>()) k_pair_density_fused(PDArgs<fl
         const C* yv = Ys + (size_t)l * nb * nv + v;
         C acc = mk<float>(0, 0);
         for (int mu = 0; mu < nb; ++mu) cfmac(acc, Ckqs[mu * nc + c], yv[(size_t)mu * nv]);
-        __nv_bfloat16 r0, r1, r2, i0, i1, i2;
-        split3_bf16(acc.x, r0, r1, r2);
-        split3_bf16(acc.y, i0, i1, i2);
         const long long t = ((long long)k * nv + v) * nc + c;
-        const long long o = (long long)(g0 + l) * a.kp2 + t;
-        a.R0[o] = __halves2bfloat162(r0, i0);
-        a.R1[o] = __halves2bfloat162(r1, i1);
-        a.R2[o] = __halves2bfloat162(r2, i2);
+        store_split2(acc.x, acc.y, a.R0, a.R1, (long long)(g0 + l) * a.kp2 + t);
     }
 }
 
@@ -661,7 +651,6 @@ cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precisio
     a.R64 = nullptr;
     a.R0 = reinterpret_cast<__nv_bfloat162*>(s.rho.p);
     a.R1 = a.R0 + (size_t)s.ngp * (s.kp / 2);
-    a.R2 = a.R1 + (size_t)s.ngp * (s.kp / 2);
     a.kp2 = s.kp / 2;
     if (gcf) {
         a.g_per_cta = gcf;

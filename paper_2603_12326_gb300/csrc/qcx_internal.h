@@ -46,7 +46,7 @@ struct QSlot {
     DevBuf kappa32;            // [ng][3] float
     DevBuf vs;                 // [ng] double, sqrt(4 pi)/|q+G|
     DevBuf vs32;               // [ng] float
-    DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: three bf16 planes [ngp][kp]
+    DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: two bf16 planes [ngp][kp]
     DevBuf eps;                // [nw][ng][ng] double2 (MIXED stores eps^T: row G', column G)
     DevBuf work;               // inverse work space
     DevBuf acc64;              // FP64 partial sums of the tensor-core chi0 (one region per CTA)
@@ -147,6 +147,9 @@ struct qcx_ctx {
     BatchPlan* batch = nullptr;    // cached plan (and captured graph) of the last batched solve
     int batch_tune = 1;            // autotune the batch tiling when a new plan is built
     double kappa_refine = 1.0e4;   // mixed inverse: FP64 diagonal correction above this kappa_1
+    long long wait_limit = 4000000000LL;  // tensor-core kernels: clock cycles before a pipeline wait gives up
+    int withhold_copies = 0;       // fault injection (tests): the per-q tensor-core kernel issues no copies
+    int chi0_products = 3;         // split-BF16 products per complex term of the mixed chi0 (3 or 4)
     MlpState* mlp = nullptr;       // surrogate network (parameters, Adam moments, work buffers)
 
     ~qcx_ctx();
@@ -177,12 +180,12 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi
 bool qcx_make_bf16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows);
 
 // persistent tensor-core chi0 over a tile list of uneven instances (chi0_tc_batch.cu).
-// maps: [nslot][3] tensor maps (box {32, 64}) of the BF16 planes of slots slot0 .. slot0 + nslot - 1;
+// maps: [nslot][2] tensor maps (box {32, 64}) of the BF16 planes of slots slot0 .. slot0 + nslot - 1;
 // tiles: {inst, gb, n0, N | src<<16}, every tile's instance in that slot range.
 cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, int slot0, int nslot, int ntile,
                                      const int4* d_tiles, int grid, const BatchInst* d_inst, const float2* wtab,
                                      long long wld, int kstages, double pref, double* acc64, double2* eps,
-                                     int* status);
+                                     int* status, long long wait_limit, int nprod);
 size_t qcx_chi0_tc_batch_acc_bytes(int grid);
 
 // batched solve for the heads of eps^-1 (batch_solve.cu)

@@ -13,7 +13,11 @@ namespace {
 
 constexpr int KSTEP = 32;                 // BF16 K elements per stage = one 64-byte swizzle row
 constexpr int ROWB = 2 * KSTEP;           // bytes per operand row in shared memory
-constexpr long long WAIT_LIMIT = 4000000000LL;  // clock cycles (~2 s)
+// Waits of the pipeline give up after a limit passed to the kernel (the
+// context's setting, ~2 s of clock cycles by default); the waits of the clean-up
+// that lets a CTA's own copies and MMAs finish before it frees TMEM and exits
+// always use this fixed bound, however short the pipeline limit is.
+constexpr long long CLEANUP_WAIT_LIMIT = 4000000000LL;  // clock cycles (~2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -39,16 +43,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait by one thread.  Returns false on timeout (which also raises
-// the CTA abort flag and the global status) or when another role aborted.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+// Bounded wait by one thread.  Returns false after `limit` clock cycles (which
+// also raises the CTA abort flag and the global status) or when another role
+// aborted.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status, long long limit,
                           bool honour_abort = true) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (honour_abort && *abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             atomicExch(status, 1);
             return false;
@@ -56,9 +61,10 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_fl
     }
 }
 // warp-uniform version: lane 0 waits, the result is broadcast
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          long long limit) {
     int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, status) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, status, limit) ? 1 : 0;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 

@@ -50,6 +50,9 @@ _SIGS = {
     "qcx_chi0": (I, [P, I, I, P, D, I, P]),
     "qcx_invert_eps": (I, [P, I, I, P, P, P]),
     "qcx_set_refine_threshold": (I, [P, D]),
+    "qcx_set_wait_limit": (I, [P, ct.c_longlong]),
+    "qcx_set_fault_injection": (I, [P, I]),
+    "qcx_set_chi0_products": (I, [P, I]),
     "qcx_loss_function": (I, [P, I, P, P]),
     "qcx_bin_loss": (I, [P, I, P, I, I, P, P, P]),
     "qcx_rate": (I, [P, I, P, I, P, P, ct.POINTER(HaloParams), P, I, P]),
@@ -236,6 +239,15 @@ class Context:
 
     def set_refine_threshold(self, kappa1):
         self._check(qcx_set_refine_threshold(self.h, float(kappa1)))
+
+    def set_wait_limit(self, cycles):
+        self._check(qcx_set_wait_limit(self.h, int(cycles)))
+
+    def set_chi0_products(self, nprod: int):
+        self._check(qcx_set_chi0_products(self.h, int(nprod)))
+
+    def set_fault_injection(self, withhold_copies: bool):
+        self._check(qcx_set_fault_injection(self.h, 1 if withhold_copies else 0))
 
     def loss_function(self, iq, prec=QCX_FP64, out_lfe=None, out_nolfe=None):
         nw, ng = self._nw[prec], self._ng[prec]

@@ -267,13 +267,14 @@ def make_surrogate_set(nq: int = 110) -> Problem:
     return p
 
 
-def make_large(nq: int | None = None, nw: int | None = None) -> Problem:
+def make_large(nq: int | None = None, nw: int | None = None, n_k: int = 12) -> Problem:
     """Large all-electron-style workload (seed 1239).  The raw draws at k+q
-    are [nq][1728][144][144] complex; ask for a few q only."""
+    are [nq][1728][144][144] complex; ask for a few q only.  `n_k` < 12 gives
+    the same basis, G set and q list on a coarser n_k^3 k grid (other draws)."""
     rng = np.random.default_rng(1239)
     cell = diamond_cell()
     basis = sp_basis(rng, 2, 18, 0.1, 5000.0)
-    kp = kgrid(cell, 12)
+    kp = kgrid(cell, n_k)
     nq_full = 100
     G = g_lowest_shells(cell, 531)
     q = random_q(rng, cell, nq_full, 6.0, G)

@@ -2,7 +2,6 @@
 declared in include/qcx.h (no GPU needed: no compute call is made)."""
 import ctypes
 import os
-import subprocess
 
 import pytest
 
@@ -25,10 +24,12 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_library_is_built_for_sm103a(lib):
-    out = subprocess.run(["cuobjdump", "--list-elf", qcx.library_path()], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    """The build compiles every source for sm_103a alone (one -gencode, no
+    PTX for other targets); on a GPU, qcx_create also refuses a library whose
+    kernels report another binary version (cudaFuncGetAttributes)."""
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    src = open(os.path.join(os.path.dirname(qcx.__file__), "csrc", "api.cu")).read()
+    assert "fa.binaryVersion != 103" in src
 
 
 def test_create_without_device_fails_cleanly(lib):

@@ -2,18 +2,27 @@
 
 A random-schedule model of the roles of k_chi0_tc (one tile per CTA) and of
 the persistent k_chi0_tc_batch (a list of tiles per CTA, stage and window
-counters running on across tiles): the TMA producer, the A-operand
-warps (which also drain the accumulators), two MMA issuers on alternate
-accumulation windows, copies that land in any order and MMAs that complete in
-issue order.  Barriers follow the mbarrier phase rule (a wait on parity p
-returns once the current phase's parity differs from p), so a wait that runs
-one phase ahead of its barrier passes early.  Every wait records the event it
-stands for; the test asserts that each wait passes only after that event,
-that no shared-memory stage or TMEM buffer is overwritten while its MMAs may
-still read it, and that every schedule finishes.  The ring depth and window
-length are read from the kernel source, so a change to either is re-checked.
-A ring of two stages, where an issuer's first wait can pass a phase early, is
-the negative control."""
+counters running on across tiles): the TMA producer, every A-operand warp
+(which also drains the accumulators; k_chi0_tc has two groups of eight warps
+taking alternate K stages, k_chi0_tc_batch one group of eight), two MMA
+issuers on alternate accumulation windows, copies that land in any order and
+MMAs that complete in issue order.  A barrier completes a phase when its
+expected number of arrivals is in (each A warp arrives on its own), and a wait
+on parity p returns once the completed-phase count's parity differs from p, so
+a wait that runs one phase ahead of its barrier passes early.  Every wait
+records the event it stands for; the test asserts that each wait passes only
+after that event, that no shared-memory stage or TMEM buffer is overwritten
+while its MMAs may still read it, that every schedule finishes, and that when
+the producer leaves no copy is in flight and when TMEM is freed no MMA is.
+The same model runs with waits that give up (a wait limit that runs out, or
+copies withheld so that nothing completes): the abort must still end every
+role with its copies landed and its MMAs finished.  Ring depths and window
+lengths are those the launchers choose (4-8 stages; 3 or 4 stages per window),
+and the kernel sources are checked for the constants the model assumes.
+The copy and A-tile barriers are indexed by the stage modulo twice the ring
+depth, so a barrier's previous phase always belongs to the same A-warp group
+and lies two windows back for an issuer.  A ring shorter than the window,
+where an issuer's wait can pass a phase early, is the negative control."""
 import os
 import random
 import re
@@ -23,146 +32,252 @@ import pytest
 CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2603_12326_gb300", "csrc")
 
 
-def _constant(name, src="chi0_tc.cu"):
-    m = re.search(r"constexpr int %s = (\d+);" % name, open(os.path.join(CSRC, src)).read())
+def _src(name):
+    return open(os.path.join(CSRC, name)).read()
+
+
+def _constant(name, src):
+    m = re.search(r"constexpr int %s = (\d+);" % name, _src(src))
     assert m, (src, name)
     return int(m.group(1))
 
 
 class _Bar:
-    def __init__(self):
-        self.done = 0
+    def __init__(self, count):
+        self.count, self.pending, self.done = count, 0, 0
 
     def arrive(self):
-        self.done += 1
+        self.pending += 1
+        assert self.pending <= self.count
+        if self.pending == self.count:
+            self.pending = 0
+            self.done += 1
 
     def passes(self, parity):
         return (self.done & 1) != parity
 
 
-def _run(kstages, nstage, promote, seed, ntile=1):
+def _run(kstages, nstage, promote, seed, ngroups=2, ntile=1, timeouts=False, withhold=False):
+    """One random schedule.  ngroups = 2: the per-q kernel (16 A warps, group g
+    forms stages g, g+2, ...; a warp drains the windows before wd after its
+    group's last stage of window wd); ngroups = 1: the batch kernel (8 A warps,
+    every stage; the previous window is drained after a window's last stage)."""
     rnd = random.Random(seed)
-    full_b = [_Bar() for _ in range(nstage)]
-    full_a = [_Bar() for _ in range(nstage)]
-    empty = [_Bar() for _ in range(nstage)]
-    acc_full = [_Bar(), _Bar()]
-    drained = [_Bar(), _Bar()]
-    landed, gen_done, mma_done, drain_done = set(), set(), set(), set()
+    nwarp = 8 * ngroups
+    # copy and A-tile barriers: one per stage modulo twice the ring depth
+    full_b = [_Bar(1) for _ in range(2 * nstage)]
+    full_a = [_Bar(8) for _ in range(2 * nstage)]
+    empty = [_Bar(1) for _ in range(nstage)]
+    acc_full = [_Bar(1), _Bar(1)]
+    drained = [_Bar(nwarp), _Bar(nwarp)]
+    mma_done_bar = _Bar(2)
+    landed, gen_done, mma_done, drain_done = set(), {}, set(), {}
     copies, mmas, errors = [], [], []
+    issued = []
+    state = {"abort": False, "producer_left": False}
     nwin = (kstages + promote - 1) // promote
+    ntot = ntile * kstages
 
-    def wait(bar, parity, event_happened, what):
+    def wait(bar, parity, event_happened, what, honour_abort=True):
+        spins = 0
         while not bar.passes(parity):
+            if honour_abort and state["abort"]:
+                return False
+            spins += 1
+            if honour_abort and timeouts and spins > 8 and rnd.random() < 0.01:
+                state["abort"] = True             # the wait limit ran out
+                return False
             yield
         if not event_happened():
             errors.append("early pass: " + what)
-
-    ntot = ntile * kstages                       # stages of all tiles of the CTA, in order
+        return True
 
     def producer():
-        for gs in range(ntot):
+        for gs in range(0 if withhold else ntot):
             s, ph = gs % nstage, (gs // nstage) & 1
-            yield from wait(empty[s], ph ^ 1, lambda gs=gs: gs < nstage or (gs - nstage) in mma_done,
-                            "stage %d free" % gs)
-            copies.append((gs, s))
+            ok = yield from wait(empty[s], ph ^ 1, lambda gs=gs: gs < nstage or (gs - nstage) in mma_done,
+                                 "stage %d free" % gs)
+            if not ok:
+                break
+            copies.append((gs, gs % (2 * nstage)))
+            issued.append(gs)
+        for gs in issued[-nstage:]:              # let the copies in flight land
+            yield from wait(full_b[gs % (2 * nstage)], (gs // (2 * nstage)) & 1, lambda gs=gs: gs in landed,
+                            "copy %d" % gs, honour_abort=False)
+        if [c for c in copies]:
+            errors.append("producer left with copies in flight")
+        state["producer_left"] = True
 
-    def a_warps():
+    def a_warp(w):
+        grp = w >> 3
+        drained_upto = 0
+
         def drain(gw):
-            yield from wait(acc_full[gw & 1], (gw >> 1) & 1, lambda: ("win", gw) in mma_done, "window %d" % gw)
-            drain_done.add(gw)
-            drained[gw & 1].arrive()
+            ok = yield from wait(acc_full[gw & 1], (gw >> 1) & 1, lambda: ("win", gw) in mma_done, "window %d" % gw)
+            if ok:
+                drain_done[gw] = drain_done.get(gw, 0) + 1
+                drained[gw & 1].arrive()
+            return ok
 
         for lt in range(ntile):
-            for it in range(kstages):
+            stages = range(grp, kstages, 2) if ngroups == 2 else range(kstages)
+            nxt = 0
+            for it in stages:
                 gs = lt * kstages + it
-                s, ph = gs % nstage, (gs // nstage) & 1
-                yield from wait(full_b[s], ph, lambda gs=gs: gs in landed, "copy %d" % gs)
+                s, ph = gs % (2 * nstage), (gs // (2 * nstage)) & 1
+                ok = yield from wait(full_b[s], ph, lambda gs=gs: gs in landed, "copy %d" % gs)
+                if not ok:
+                    return
                 if gs >= nstage and (gs - nstage) not in mma_done:
                     errors.append("A tile %d overwritten under its MMAs" % gs)
-                gen_done.add(gs)
+                gen_done[gs] = gen_done.get(gs, 0) + 1
                 full_a[s].arrive()
-                # drain the previous window after the last stage of a window; at the tile's end the rest
-                wd0, wd1 = nwin, -1
-                if it % promote == promote - 1 and it >= promote:
-                    wd0 = wd1 = it // promote - 1
-                if it + 1 == kstages:
-                    wd0 = min(wd0, it // promote - 1 if (it % promote == promote - 1 and it >= promote)
-                              else max(nwin - 2, 0))
-                    wd1 = nwin - 1
-                for wd in range(wd0, wd1 + 1):
-                    yield from drain(lt * nwin + wd)
+                if ngroups == 2:
+                    wd = it // promote
+                    if it + 2 >= min((wd + 1) * promote, kstages):
+                        while nxt < wd:
+                            ok = yield from drain(lt * nwin + nxt)
+                            nxt += 1
+                            if not ok:
+                                return
+                else:
+                    wd0, wd1 = nwin, -1
+                    if it % promote == promote - 1 and it >= promote:
+                        wd0 = wd1 = it // promote - 1
+                    if it + 1 == kstages:
+                        wd0 = min(wd0, it // promote - 1 if (it % promote == promote - 1 and it >= promote)
+                                  else max(nwin - 2, 0))
+                        wd1 = nwin - 1
+                    for wd in range(wd0, wd1 + 1):
+                        ok = yield from drain(lt * nwin + wd)
+                        if not ok:
+                            return
+                    nxt = nwin
+            while nxt < nwin:
+                ok = yield from drain(lt * nwin + nxt)
+                nxt += 1
+                if not ok:
+                    return
 
     def issuer(par):
+        ok = True
         for lt in range(ntile):
             for wd in range(nwin):
                 gw = lt * nwin + wd
-                if (gw & 1) != par:
+                if (gw & 1) != par or not ok:
                     continue
                 b = gw & 1
                 if gw >= 2:
-                    yield from wait(drained[b], ((gw - 2) >> 1) & 1, lambda g=gw: (g - 2) in drain_done,
-                                    "buffer of window %d drained" % gw)
+                    ok = yield from wait(drained[b], ((gw - 2) >> 1) & 1,
+                                         lambda g=gw: drain_done.get(g - 2, 0) == nwarp,
+                                         "buffer of window %d drained" % gw)
+                    if not ok:
+                        break
                 for it in range(wd * promote, min((wd + 1) * promote, kstages)):
                     gs = lt * kstages + it
-                    s = gs % nstage
-                    yield from wait(full_a[s], (gs // nstage) & 1, lambda gs=gs: gs in gen_done, "A tile %d" % gs)
+                    s2 = gs % (2 * nstage)
+                    ok = yield from wait(full_a[s2], (gs // (2 * nstage)) & 1,
+                                         lambda gs=gs: gen_done.get(gs, 0) == 8, "A tile %d" % gs)
+                    if not ok:
+                        break
                     if gs not in landed:
                         errors.append("MMA %d before its copy landed" % gs)
-                    mmas.append((gs, [empty[s]]))
+                    mmas.append((gs, [empty[gs % nstage]]))
                     yield
-                mmas.append((("win", gw), [acc_full[b]]))
+                if ok:
+                    mmas.append((("win", gw), [acc_full[b]]))
                 yield
+        mmas.append((("done", par), [mma_done_bar]))
+        yield from wait(mma_done_bar, 0, lambda: ("done", 0) in mma_done and ("done", 1) in mma_done,
+                        "every MMA finished", honour_abort=False)
 
-    actors = [producer(), a_warps(), issuer(0), issuer(1)]
+    actors = [producer(), issuer(0), issuer(1)] + [a_warp(w) for w in range(nwarp)]
     alive = [True] * len(actors)
-    for _ in range(400000):
-        if not any(alive) and not copies and not mmas:
-            return errors, (len(gen_done), len(drain_done))
+    for _ in range(2000000):
+        if not any(alive):
+            if mmas:
+                errors.append("TMEM freed with MMAs in flight")
+            if not state["abort"] and (len(gen_done) != ntot or len(drain_done) != ntile * nwin):
+                errors.append("work missing without an abort")
+            if withhold and not state["abort"]:
+                errors.append("withheld copies did not abort the kernel")
+            return errors, state["abort"]
         r = rnd.random()
-        if r < 0.2 and copies:
-            it, s = copies.pop(rnd.randrange(len(copies)))       # copies land in any order
-            landed.add(it)
-            full_b[s].arrive()
-        elif r < 0.4 and mmas:
+        if r < 0.15 and copies:
+            gs, s2 = copies.pop(rnd.randrange(len(copies)))      # copies land in any order
+            landed.add(gs)
+            full_b[s2].arrive()
+        elif r < 0.3 and mmas:
             key, bars = mmas.pop(0)                               # MMAs complete in issue order
             mma_done.add(key)
             for bar in bars:
                 bar.arrive()
         else:
             live = [i for i, a in enumerate(alive) if a]
-            if live:
-                i = rnd.choice(live)
-                try:
-                    next(actors[i])
-                except StopIteration:
-                    alive[i] = False
+            i = rnd.choice(live)
+            try:
+                next(actors[i])
+            except StopIteration:
+                alive[i] = False
     return errors + ["no progress (deadlock)"], None
 
 
-@pytest.mark.parametrize("kstages", [1, 2, 3, 5, 8, 63])
-def test_kernel_protocol_holds_under_random_schedules(kstages):
-    nstage, promote = _constant("NSTAGE"), _constant("PROMOTE")
-    for seed in range(60):
-        errors, counts = _run(kstages, nstage, promote, seed)
-        assert not errors, (nstage, promote, kstages, seed, errors[:3])
-        nwin = (kstages + promote - 1) // promote
-        assert counts == (kstages, nwin)
+def test_model_matches_the_kernel_sources():
+    """The constants and counts the model assumes are those of the kernels."""
+    src = _src("chi0_tc.cu")
+    assert _constant("NAW", "chi0_tc.cu") == 16 and _constant("MAXSTAGE", "chi0_tc.cu") == 8
+    assert "mbar_init(&full_a[s], 8)" in src and "mbar_init(&drained[b], NAW)" in src
+    assert "for (int s = 0; s < 2 * NS; ++s)" in src            # copy and A-tile barriers: 2 NS of each
+    assert src.count("% (2 * NS)") >= 4 and "&empty[s]" in src
+    assert "for (int it = grp; it < a.kstages && ok; it += 2)" in src
+    assert "if (it + 2 >= min((wd + 1) * a.promote, a.kstages))" in src
+    assert "for (int it = max(0, last - NS + 1); it <= last; ++it)" in src
+    assert _constant("WIN_MMAS", "chi0_tc.cu") == 24
+    assert "a.promote = WIN_MMAS / ((KSTEP / 16) * a.nprod)" in src and "a.nstage < 4" in src
+    bsrc = _src("chi0_tc_batch.cu")
+    assert _constant("NSTAGE", "chi0_tc_batch.cu") == 4
+    assert "mbar_init(&full_a[s], 8)" in bsrc and "mbar_init(&drained[b], 8)" in bsrc
+    assert bsrc.count("% (2 * NSTAGE)") >= 4
+    assert "a.promote = 24 / ((KSTEP / 16) * nprod)" in bsrc
+
+
+@pytest.mark.parametrize("nstage", [4, 5, 6, 8])
+@pytest.mark.parametrize("promote", [3, 4])
+@pytest.mark.parametrize("kstages", [1, 2, 3, 5, 8, 13, 40])
+def test_kernel_protocol_holds_under_random_schedules(nstage, promote, kstages):
+    for seed in range(8):
+        errors, aborted = _run(kstages, nstage, promote, seed)
+        assert not errors and not aborted, (nstage, promote, kstages, seed, errors[:3])
+
+
+@pytest.mark.parametrize("nstage,promote", [(4, 4), (5, 3), (5, 4), (8, 3)])
+def test_kernel_abort_path_drains_copies_and_mmas(nstage, promote):
+    """Waits that give up at random points (or copies withheld, so that the
+    first waits run out): every role ends, the producer leaves no copy in
+    flight and no MMA runs when TMEM is freed."""
+    n_abort = 0
+    for seed in range(40):
+        errors, aborted = _run(24, nstage, promote, seed, timeouts=True)
+        assert not errors, (seed, errors[:3])
+        n_abort += bool(aborted)
+        errors, aborted = _run(9, nstage, promote, seed, timeouts=True, withhold=True)
+        assert not errors and aborted, (seed, errors[:3])
+    assert n_abort > 0
 
 
 @pytest.mark.parametrize("kstages,ntile", [(1, 5), (2, 4), (3, 3), (5, 3), (8, 2), (13, 3)])
-def test_batch_kernel_protocol_across_tiles(kstages, ntile):
+@pytest.mark.parametrize("promote", [3, 4])
+def test_batch_kernel_protocol_across_tiles(kstages, ntile, promote):
     """The persistent batch kernel runs the same roles over a list of tiles with
     the stage and window counters continuing across tiles."""
-    nstage, promote = _constant("NSTAGE", "chi0_tc_batch.cu"), _constant("PROMOTE", "chi0_tc_batch.cu")
-    for seed in range(40):
-        errors, counts = _run(kstages, nstage, promote, seed, ntile=ntile)
-        assert not errors, (kstages, ntile, seed, errors[:3])
-        nwin = (kstages + promote - 1) // promote
-        assert counts == (kstages * ntile, nwin * ntile)
+    nstage = _constant("NSTAGE", "chi0_tc_batch.cu")
+    for seed in range(10):
+        errors, aborted = _run(kstages, nstage, promote, seed, ngroups=1, ntile=ntile)
+        assert not errors and not aborted, (kstages, ntile, seed, errors[:3])
 
 
-def test_two_stage_ring_is_caught():
-    """With two stages the second issuer's first wait (stage 2, the second use
-    of its barrier) can pass before stage 0's tile exists."""
-    bad = sum(bool(_run(16, 2, 2, seed)[0]) for seed in range(40))
+def test_short_ring_is_caught():
+    """A window longer than the ring (five stages per window on a ring of
+    two) lets an issuer's wait on an A-tile barrier pass one phase early."""
+    bad = sum(bool(_run(20, 2, 5, seed, ngroups=1)[0]) for seed in range(20))
     assert bad > 0

@@ -59,3 +59,33 @@ def test_mid_workload_full_size_fp64(mid):
     ctx.close()
     assert rel(chi, o["chi0"]) < 1e-10
     assert rel(L1, o["L_lfe"]) < 1e-10 and rel(L2, o["L_nolfe"]) < 1e-10
+
+
+def test_mid_workload_every_q_mixed_vs_fp64_gpu():
+    """All 50 q of the benchmark workload: the mixed path's loss tables (all
+    200 w in one launch per q, as the benchmark runs them) against the FP64 GPU
+    path (itself held to 1e-10 of the oracle) at eight frequencies per q.
+    Bar: 1e-4 relative per spectrum (fixed q and G) where L exceeds 1e-3 of the
+    spectrum's maximum over the 200 frequencies."""
+    from paper_2603_12326_gb300 import states
+    p = synth.make_mid()
+    ctx = context()
+    states.load_problem(ctx, p)
+    sample = np.linspace(1, len(p.w) - 1, 8).astype(int)
+    worst = {"L_lfe": 0.0, "L_nolfe": 0.0}
+    for iq in range(p.nq):
+        ctx.pair_density(iq, p.G_int, QCX_MIXED)
+        ctx.chi0(iq, p.w, p.eta, QCX_MIXED)
+        ctx.invert_eps(iq, QCX_MIXED, want=False)
+        m1, m2 = ctx.loss_function(iq, QCX_MIXED)
+        ctx.pair_density(iq, p.G_int, QCX_FP64)
+        ctx.chi0(iq, p.w[sample], p.eta, QCX_FP64)
+        ctx.invert_eps(iq, QCX_FP64, want=False)
+        d1, d2 = ctx.loss_function(iq, QCX_FP64)
+        for key, m, d in (("L_lfe", m1, d1), ("L_nolfe", m2, d2)):
+            top = np.max(np.abs(m), axis=0, keepdims=True)
+            mask = np.abs(d) > 1e-3 * top
+            worst[key] = max(worst[key], float(np.max(np.abs(m[sample][mask] - d[mask]) / np.abs(d[mask]))))
+    ctx.close()
+    print("mid workload, 50 q x 8 w, mixed vs FP64 GPU:", {k: f"{v:.2e}" for k, v in worst.items()})
+    assert worst["L_lfe"] < 1e-4 and worst["L_nolfe"] < 1e-4

@@ -15,7 +15,7 @@ import pytest
 import synth
 from oracle import rpa
 from paper_2603_12326_gb300 import QCX_MIXED
-from tests.gpu_util import context, set_oracle_states
+from tests.gpu_util import context, rel_spectrum, set_oracle_states
 
 pytestmark = pytest.mark.gpu
 SAMPLE_G = np.array([0, 1, 100, 530])
@@ -60,3 +60,37 @@ def test_large_workload_full_size_mixed(large):
     assert e_chi < 5e-5 and e2 < 1e-4
     assert np.all(np.isfinite(L1)) and np.all(np.isfinite(L2))
     assert np.all(L1[1:] > -1e-8) and np.all(L2[1:] > -1e-8)
+
+
+@pytest.fixture(scope="module")
+def large_k4():
+    """The large workload's basis (18 sp shells per atom up to 5000 bohr^-2,
+    N_b = 144), bands (N_v = 14, N_c = 64), G set (N_G = 531), first q and
+    eta on a 4^3 k grid (N_t = 57 344), where the oracle can form the whole
+    problem at four frequencies."""
+    p = synth.make_large(nq=1, n_k=4)
+    Ck, Ckq = rpa.states(p, 0)
+    o = rpa.solve_q(p, 0, Ck, Ckq, w=p.w[SAMPLE_W])
+    return p, Ck, Ckq, o
+
+
+def test_large_basis_full_loss_tables_vs_oracle(large_k4):
+    """Every G of both loss tables at the four sampled frequencies, mixed path
+    in one launch over all 400 w, against the oracle's full N_G = 531 inverse:
+    L_LFE is where the inverse amplifies the contraction's error most (core
+    exponents up to 5000 bohr^-2, eta = 0.05 eV).  Bar: 1e-4 relative per
+    spectrum where L > 1e-3 of its maximum over the sampled frequencies."""
+    p, Ck, Ckq, o = large_k4
+    assert p.G_int.shape[0] == 531 and p.nt == 57344
+    ctx = context()
+    set_oracle_states(ctx, p, [0], Ck, [Ckq])
+    ctx.pair_density(0, p.G_int, QCX_MIXED)
+    chi = ctx.chi0(0, p.w, p.eta, QCX_MIXED, want=True)
+    ctx.invert_eps(0, QCX_MIXED, want=False)
+    L1, L2 = ctx.loss_function(0, QCX_MIXED)
+    ctx.close()
+    e_chi = float(np.max(np.abs(chi[SAMPLE_W] - o["chi0"])) / np.max(np.abs(o["chi0"])))
+    e1 = rel_spectrum(L1[SAMPLE_W], o["L_lfe"])
+    e2 = rel_spectrum(L2[SAMPLE_W], o["L_nolfe"])
+    print(f"large basis, 4^3 k, mixed: chi0 {e_chi:.2e}, L_LFE {e1:.2e}, L_noLFE {e2:.2e}")
+    assert e_chi < 5e-5 and e1 < 1e-4 and e2 < 1e-4

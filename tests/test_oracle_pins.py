@@ -520,3 +520,26 @@ def test_loss_as_quadratic_form_of_the_anti_hermitian_part():
         assert np.allclose(quad.real, o["L_lfe"], rtol=1e-10, atol=1e-14)
         bad = np.einsum("wkj,wkl,wjl->wj", X, B, np.conj(X))
         assert not np.allclose(bad.real, o["L_lfe"], rtol=1e-3)
+
+
+def test_bin_loss_by_hand():
+    """The |q| binning that feeds the rate integral (the momentum grid of the
+    q integral of the rate, Appendix A): bins are half-open [e_i, e_(i+1)), a
+    value on an inner edge belongs to the bin above it, values on or past the
+    last edge and below the first are dropped, a bin holds the MEAN of its
+    rows (not their sum), an empty bin is 0, and the centres are the edge
+    midpoints.  Expected values are written out by hand."""
+    edges = np.array([0.0, 0.1, 0.2, 0.3, 0.4])
+    qmag = np.array([0.05, 0.1, 0.15, 0.35, 0.4, 0.5, -0.01, 0.0])
+    L = np.array([[1.0, 10.0],       # 0.05 -> bin 0
+                  [2.0, 20.0],       # 0.1 (inner edge) -> bin 1
+                  [4.0, 40.0],       # 0.15 -> bin 1
+                  [8.0, 80.0],       # 0.35 -> bin 3
+                  [16.0, 160.0],     # 0.4 (last edge) -> dropped
+                  [32.0, 320.0],     # past the last edge -> dropped
+                  [64.0, 640.0],     # below the first edge -> dropped
+                  [128.0, 1280.0]])  # 0.0 (first edge) -> bin 0
+    out, centres, cnt = rate.bin_loss(qmag, L, edges)
+    assert np.array_equal(cnt, [2, 2, 0, 1])
+    assert np.array_equal(out, [[64.5, 645.0], [3.0, 30.0], [0.0, 0.0], [8.0, 80.0]])
+    assert np.allclose(centres, [0.05, 0.15, 0.25, 0.35], rtol=0, atol=1e-15)
