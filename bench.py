@@ -10,8 +10,10 @@ region; the per-q R planes (150 MB) and states (1.3 GB) exceed the 129 MB
 L2, so no separate L2 flush is done.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun (N > 1) every rank processes its own 50-q shard (weak scaling,
-no data-path collective); the timing is the max over ranks.
+Under torchrun (N > 1) every rank processes its own 50-q shard (weak scaling);
+the |q+G| bins of the loss tables are summed over the ranks by one all-reduce
+(the path's only exchange) and rank 0 evaluates the rate; the timing is the
+max over ranks.  Run without a launcher, --gpus N starts the N ranks itself.
 """
 from __future__ import annotations
 
@@ -207,7 +209,7 @@ def run_ours(args, ws, rank, local):
     import torch
 
     import synth
-    from paper_2603_12326_gb300 import QCX_FP64, QCX_MIXED, qcx, states
+    from paper_2603_12326_gb300 import QCX_FP64, QCX_MIXED, qcx, shards, states
     from paper_2603_12326_gb300.build import build
 
     build()
@@ -230,9 +232,9 @@ def run_ours(args, ws, rank, local):
 
     chi_events = []
     pd_events = []
-    # algorithmic bytes of one pair-density launch: the FP32 coefficients read once, the three BF16 planes of
+    # algorithmic bytes of one pair-density launch: the FP32 coefficients read once, the two BF16 planes of
     # rho written once
-    pd_bytes = 8.0 * prob.nk * prob.basis.nbasis * (prob.nv + prob.nc) + 12.0 * nt * ng
+    pd_bytes = 8.0 * prob.nk * prob.basis.nbasis * (prob.nv + prob.nc) + 8.0 * nt * ng
 
     def step(record=False):
         for iq in range(nq):
@@ -254,7 +256,13 @@ def run_ours(args, ws, rank, local):
                 chi_events.append((e0, e1))
             ctx.invert_eps(iq, QCX_MIXED, want=False)
         Lb, cnt = ctx.bin_loss(list(range(nq)), 0, edges, nw)
-        Lb2, _ = ctx.bin_loss(list(range(nq)), 1, edges, nw)
+        Lb2, cnt2 = ctx.bin_loss(list(range(nq)), 1, edges, nw)
+        if ws > 1:
+            # the one exchange of the path: the |q+G| bins of every rank's q, summed over the ranks
+            Lb, cnt = shards.combine_bins(Lb, cnt, device=f"cuda:{local}")
+            Lb2, _ = shards.combine_bins(Lb2, cnt2, device=f"cuda:{local}")
+            if rank != 0:
+                return None, None
         nz = cnt > 0
         qb = 0.5 * (edges[1:] + edges[:-1])[nz]
         dR, dQ = ctx.rate(qb, w, Lb[nz], halo, nQ=10)
@@ -309,6 +317,10 @@ def run_ours(args, ws, rank, local):
             ctx.invert_eps(iq, QCX_MIXED, want=False)
             ctx.loss_function(iq, QCX_MIXED, out_lfe=outL[iq, 0].numpy(), out_nolfe=outL[iq, 1].numpy())
         Lb, cnt = ctx.bin_loss(list(range(nq)), 0, edges, nw)
+        if ws > 1:
+            Lb, cnt = shards.combine_bins(Lb, cnt, device=f"cuda:{local}")
+            if rank != 0:
+                return
         nz = cnt > 0
         ctx.rate(0.5 * (edges[1:] + edges[:-1])[nz], w, Lb[nz], halo, nQ=10)
 
@@ -354,6 +366,7 @@ def run_ours(args, ws, rank, local):
 
     # ------------------------------------------- batched uneven instances (rank 0, N=1)
     batched = batched_leg(stream) if (rank == 0 and ws == 1) else None
+    large = large_leg(stream, args.products) if (rank == 0 and ws == 1 and not args.no_large) else None
     surro = surrogate_leg(stream) if (rank == 0 and ws == 1 and not args.no_surrogate) else None
 
     # -------------------------------------------------------- CPU oracle (rank 0, N=1)
@@ -409,6 +422,8 @@ def run_ours(args, ws, rank, local):
             out["cpu_baseline"] = cpu
         if batched:
             out["batched"] = batched
+        if large:
+            out["large"] = large
         if surro:
             out["surrogate"] = surro
         print(json.dumps(out), flush=True)
@@ -458,6 +473,85 @@ def accuracy_sweep(ctx, prob, G, w, eta, outL, nsample=8):
             "vs": "FP64 GPU path (held to 1e-10 of the oracle)",
             "sample": f"all {prob.nq} q x {nsample} w of the timed workload, every G; per spectrum where "
                       f"L > 1e-3 of its maximum over the {len(w)} w"}
+
+
+def large_leg(stream, products, nq=2, nk_oracle=8):
+    """The large all-electron workload (18 sp shells per atom up to 5000 bohr^-2,
+    12^3 k, N_v = 14, N_c = 64: N_t = 1 548 288, N_G = 531, 400 w on 0-100 eV,
+    eta = 0.05 eV) through the mixed path for its first nq q (every q costs the
+    same): blocks/s over the per-q path (pair densities, chi0 with the Dyson
+    step, inverse and loss tables), the chi0 launch's algorithmic rate against
+    the sustained peak, the FP64 recoil spectrum of those q, and the oracle on
+    a bounded sample (nk_oracle of the 1728 k points, 1 q x 4 w)."""
+    import torch
+
+    import synth
+    from paper_2603_12326_gb300 import QCX_MIXED, qcx, states
+
+    ctx = qcx.Context(torch.cuda.current_device(), stream=stream.cuda_stream)
+    ctx.set_chi0_products(products)
+    p = synth.make_large(nq=nq)
+    Ck, Ckq = states.load_problem(ctx, p)
+    G, w = p.G_int, p.w
+    ng, nw, nt = p.ng, len(w), p.nt
+    ctx.pair_density(0, G, QCX_MIXED)                      # warm-up (kernel attributes, buffers)
+    ctx.chi0(0, w[:8], p.eta, QCX_MIXED)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nq + 2)]
+    chi = []
+    ev[0].record(stream)
+    for iq in range(nq):
+        ctx.pair_density(iq, G, QCX_MIXED)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        ctx.chi0(iq, w, p.eta, QCX_MIXED)
+        c1.record(stream)
+        chi.append((c0, c1))
+        ctx.invert_eps(iq, QCX_MIXED, want=False)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    chi_ms = float(np.mean([a.elapsed_time(b) for a, b in chi]))
+    flops = 8.0 * nt * ng * ng * nw
+    peak = _peaks().get("bf16_tflops_sustained", 1700.0)
+    edges = np.linspace(0.0, 16.0, 161)
+    halo = qcx.halo_params()
+    Lb, cnt = ctx.bin_loss(list(range(nq)), 0, edges, nw)
+    nz = cnt > 0
+    dR, dQ = ctx.rate(0.5 * (edges[1:] + edges[:-1])[nz], w, Lb[nz], halo, nQ=10)
+    L1, _ = ctx.loss_function(0, QCX_MIXED)
+    ctx.close()
+    # the oracle on a bounded sample of the same workload
+    from oracle import rpa
+    c, b = p.cell, p.basis
+    kap = p.qpts[0][None, :] + G @ c.recip
+    ws_ = w[np.linspace(1, nw - 1, 4).astype(int)]
+    t0 = time.perf_counter()
+    rho = rpa.pair_density_lean(c.lattice, c.atoms, b.shell_atom, b.shell_l, b.shell_exp, p.kpts[:nk_oracle], kap,
+                                Ck[:nk_oracle], Ckq[0][:nk_oracle])
+    t1 = time.perf_counter()
+    W = rpa.transition_weights(rpa.transition_energies(p.Ek[:nk_oracle], p.Ekq[0][:nk_oracle]), ws_, p.eta)
+    eps = rpa.dielectric_matrix(rpa.chi0(rho, W, p.nk, c.volume), rpa.coulomb_sqrt(p.qpts[0], G @ c.recip))
+    rpa.loss_functions(eps)
+    t2 = time.perf_counter()
+    scale = p.nk / nk_oracle
+    per_block = (t1 - t0) * scale / nw + (t2 - t1) * scale / len(ws_)
+    return {"workload": "large: diamond a=5.43 A, 18 sp shells/atom up to 5000 bohr^-2 (N_b=144), 12x12x12 k, "
+                        "N_v=14, N_c=64 (N_t=1548288), N_G=531, 400 w on 0-100 eV, eta=0.05 eV",
+            "q_timed": nq, "value": nq * nw / (ms / 1e3), "unit": "blocks/s", "ms_per_q": ms / nq,
+            "chi0": {"kernel": "k_chi0_tc", "avg_launch_ms": chi_ms, "flops_per_launch": flops,
+                     "achieved_tflops": flops / (chi_ms / 1e3) / 1e12, "peak": peak,
+                     "frac": flops / (chi_ms / 1e3) / 1e12 / peak,
+                     "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)"},
+            "recoil_spectrum_events_per_kg_yr": [float(x) for x in dQ],
+            "recoil_spectrum_note": f"FP64 rate over the |q+G| bins of the {nq} timed q (heavy mediator, "
+                                    f"m_chi = 1 GeV)",
+            "loss_table_finite": bool(np.all(np.isfinite(L1))),
+            "cpu_baseline": {"value": 1.0 / per_block, "unit": "blocks/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"1 q: pair densities for {nk_oracle}/{p.nk} k and chi0+eps+inverse+loss for "
+                                       f"4/{nw} w over those transitions, scaled linearly in k",
+                             "seconds": round(t2 - t0, 2)}}
 
 
 def batched_leg(stream, reps=10):
@@ -643,6 +737,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-correction leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the accuracy sweep over every q")
+    ap.add_argument("--no-large", action="store_true", help="skip the large-workload leg")
     ap.add_argument("--products", type=int, default=3, choices=[3, 4],
                     help="split-BF16 products of the mixed chi0 (3: a0b0+a0b1+a1b0, 4: also a1b1)")
     ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "mid200", "batch", "mlp"],

@@ -94,8 +94,9 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& p0, uint32_t&
     p1 = pack_bf16(a - hf.x, b - hf.y);
 }
 
-// 19 warps, one CTA per SM: 104 registers per thread fit the register file
-__global__ void __maxnreg__(104)
+// 19 warps, one CTA per SM: an SM sub-partition holds 16384 registers and five of the warps, so at most
+// 96 registers per thread
+__global__ void __maxnreg__(96)
     k_chi0_tc(const __grid_constant__ CUtensorMap mb0, const __grid_constant__ CUtensorMap mb1,
               const __grid_constant__ CUtensorMap ms0, const __grid_constant__ CUtensorMap ms1, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];

@@ -1,7 +1,9 @@
-"""The N > 1 benchmark path on CPU: two gloo ranks run the benchmark's barrier
-and max-over-ranks timing, and the whole-job rate counts every rank's blocks
-over the slowest rank's time; the shards are disjoint q sets over the same k
-states (weak scaling, no data-path collective)."""
+"""The N > 1 path on CPU (two gloo ranks): the benchmark's barrier and
+max-over-ranks timing, the whole-job rate over the slowest rank's time, the
+disjoint q shards over the same k states (weak scaling), and the one data
+exchange: each rank bins the loss tables of its own q, the bin sums and
+counts are combined by an all-reduce, and the rate of the combined table
+equals the rate of the union binned on one rank."""
 import os
 import socket
 import tempfile
@@ -48,6 +50,51 @@ def test_two_gloo_ranks_share_the_max_time():
     for mx, value in res:
         assert mx == 150.0
         assert value == pytest.approx(2 * 50 * 200 * 3 / 0.150)
+
+
+def _bins_rank(rank, port, outdir, tables, qmag, edges, w):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2",
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+
+    from oracle import rate as orate
+    from paper_2603_12326_gb300 import shards
+    dist.init_process_group("gloo")
+    try:
+        mine = [i for i in range(len(tables)) if i % 2 == rank]       # rank r holds q number r, r + 2, ...
+        L = np.concatenate([tables[i] for i in mine], axis=0)
+        q = np.concatenate([qmag[i] for i in mine])
+        m, _, c = orate.bin_loss(q, L, edges)
+        gm, gc = shards.combine_bins(m, c)
+        nz = gc > 0
+        centres = 0.5 * (edges[1:] + edges[:-1])
+        dR = orate.dR_dw(centres[nz], w, gm[nz], orate.HaloParams()) if rank == 0 else np.zeros(len(w))
+        np.savez(os.path.join(outdir, f"b{rank}.npz"), mean=gm, count=gc, dR=dR)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_loss_bins_combined_over_two_ranks_equal_one_rank():
+    from oracle import rate as orate
+    from oracle import rpa
+    p = synth.make_small(nq=4, nw=30)
+    tables, qmag = [], []
+    for iq in range(4):
+        o = rpa.solve_q(p, iq)
+        tables.append(o["L_lfe"].T)                   # [(G)][w]
+        qmag.append(np.linalg.norm(p.qpts[iq][None, :] + p.G_int @ p.cell.recip, axis=1))
+    edges = np.linspace(0.0, 2.5, 13)
+    m1, centres, c1 = orate.bin_loss(np.concatenate(qmag), np.concatenate(tables, axis=0), edges)
+    nz = c1 > 0
+    dR1 = orate.dR_dw(centres[nz], p.w, m1[nz], orate.HaloParams())
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_bins_rank, args=(_free_port(), d, tables, qmag, edges, p.w), nprocs=2, join=True,
+                           start_method="spawn")
+        got = [np.load(os.path.join(d, f"b{r}.npz")) for r in range(2)]
+    for g in got:
+        assert np.array_equal(g["count"], c1)
+        assert np.allclose(g["mean"], m1, rtol=1e-12, atol=1e-14 * np.max(m1))     # summation order only
+    assert np.allclose(got[0]["dR"], dR1, rtol=1e-12, atol=0) and np.max(dR1) > 0
 
 
 def test_shards_are_disjoint_q_sets_over_the_same_k_states():
