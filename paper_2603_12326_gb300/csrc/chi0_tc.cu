@@ -9,11 +9,15 @@
 //   A[(w,re,G')][2t+p]   = (Re, Im) (W_t(w) rho_t(G'))                      (generated in shared memory)
 //   A[(w,im,G')][2t+p]   = (Im, -Re)(W_t(w) rho_t(G')),
 // so the re rows of D hold Re chi0_GG' and the im rows Im chi0_GG'.  Both
-// operands are split into two BF16 terms x = x0 + x1 (x0 = bf16(x),
-// x1 = bf16(x - x0)), and D accumulates in FP32 the three products
-// a0 b0 + a0 b1 + a1 b0 (the split-precision product with three terms), or,
-// when the context asks for it, the fourth term a1 b1 as well.  Each term is
-// an exact BF16 product; what the split leaves out is of relative order 2^-16.
+// operands are split into two FP16 terms x = x0 + x1 (x0 = fp16(x),
+// x1 = fp16(x - x0), 22 significant bits together), and D accumulates in FP32
+// the three products a0 b0 + a0 b1 + a1 b0 (the split-precision product with
+// three terms), or, when the context asks for it, the fourth term a1 b1 as
+// well.  Each term is an exact FP16 product; what the split leaves out is of
+// relative order 2^-21.  The FP16 range is kept by powers of two: the stored
+// pair densities are 2^15 rho (|rho| <= 1 for orthonormal states), and the W
+// table carries s_A 2^-15 with s_A = 2^floor(log2(8192 eta)), so that
+// |W rho s_A| <= (2/eta) 8192 eta 1.99 < 2^15; the epilogue divides by s_A 2^15.
 // W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is tabulated per q by
 // k_weights with dE and w -+ dE in FP64 and fetched with each K stage.
 //
@@ -43,7 +47,7 @@
 
 namespace {
 
-constexpr int NPIECE = 2;                 // BF16 terms per operand
+constexpr int NPIECE = 2;                 // FP16 terms per operand
 constexpr int AW0 = 3;                    // first A/drain/epilogue warp
 constexpr int NAW = 16;                   // A/drain/epilogue warps: two groups of eight
 constexpr int NTHREADS = (AW0 + NAW) * 32;
@@ -80,19 +84,6 @@ struct TcArgs {
     long long wait_limit;   // clock cycles before a pipeline wait gives up
     int withhold;           // fault injection: issue no copies
 };
-
-__device__ __forceinline__ uint32_t perm_im(uint32_t re) {
-    // (xr, xi) terms -> (xi, -xr) terms: swap the halves, negate the new high half
-    return __byte_perm(re, 0u, 0x1032) ^ 0x80000000u;
-}
-
-// (a, b) -> two packed BF16 pairs with a = a0 + a1, b = b0 + b1
-__device__ __forceinline__ void split2(float a, float b, uint32_t& p0, uint32_t& p1) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    p0 = *reinterpret_cast<const uint32_t*>(&h);
-    p1 = pack_bf16(a - hf.x, b - hf.y);
-}
 
 // 19 warps, one CTA per SM: an SM sub-partition holds 16384 registers and five of the warps, so at most
 // 96 registers per thread
@@ -219,10 +210,10 @@ __global__ void __maxnreg__(96)
 #pragma unroll
                     for (int kk = 0; kk < KSTEP / 16; ++kk) {
                         const uint32_t off = kk * 32;
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                        if (a.nprod == 4) umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                        umma_f16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
+                        umma_f16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                        umma_f16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                        if (a.nprod == 4) umma_f16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
                     }
                     umma_commit(&empty[s]);
                 }
@@ -314,10 +305,10 @@ __global__ void __maxnreg__(96)
                                       make_float2(wb4.x, wb4.y), make_float2(wb4.z, wb4.w)};
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
-                    const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]);
+                    const float2 f0 = h2f(v0[qq]), f1 = h2f(v1[qq]);
                     const float rr = f0.x + f1.x, ri = f0.y + f1.y;
                     const float2 wq = Wv[qq];
-                    split2(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq]);
+                    split2_h(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq]);
                 }
             }
             unsigned char* ap = st + aoff;
@@ -369,10 +360,10 @@ __global__ void __maxnreg__(96)
     }
 }
 
-// W[w][t] = 1/(w - dE + i eta) - 1/(w + dE + i eta), dE = E_c(k+q) - E_v(k), with dE and
+// W[w][t] = scale (1/(w - dE + i eta) - 1/(w + dE + i eta)), dE = E_c(k+q) - E_v(k), with dE and
 // w -+ dE formed in FP64; zero for padded t.
 __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, const double* Ek, const double* Ekq,
-                          const double* w, double eta, float2* W) {
+                          const double* w, double eta, double scale, float2* W) {
     const long long n = (long long)nw * ld;
     const int nvc = nv * nc;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -386,7 +377,7 @@ __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, co
             const double dE = Ekq[k * nc + c] - Ek[k * nv + vv];
             const double x1 = w[iw] - dE, x2 = w[iw] + dE;
             const double n1 = x1 * x1 + eta * eta, n2 = x2 * x2 + eta * eta;
-            const double r = 1.0 / (n1 * n2);         // one FP64 division for both denominators
+            const double r = scale / (n1 * n2);       // one FP64 division for both denominators
             const double d1 = n2 * r, d2 = n1 * r;
             v = make_float2((float)(x1 * d1 - x2 * d2), (float)(eta * (d2 - d1)));
         }
@@ -413,14 +404,14 @@ static PFN_encodeTiled_t get_encode() {
     return fn;
 }
 
-bool qcx_make_bf16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows) {
+bool qcx_make_f16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows) {
     PFN_encodeTiled_t enc = get_encode();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
     const cuuint32_t box[2] = {(cuuint32_t)KSTEP, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -455,7 +446,8 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     const double* L = ctx->lattice;
     const double vol = fabs(L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
                             L[2] * (L[3] * L[7] - L[4] * L[6]));
-    a.pref = 2.0 / (ctx->nk * vol);
+    const double s_a = qcx_w_scale(s.eta);            // power of two: exact
+    a.pref = 2.0 / (ctx->nk * vol) / (s_a * 32768.0);
     a.vs = s.vs.as<double>();
     a.eps = s.eps.as<double2>();
     a.chi = chi;
@@ -480,7 +472,8 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
         const long long n = (long long)s.nw * (s.kp / 2);
         k_weights<<<(int)std::min<long long>((n + 255) / 256, 8192), 256, 0, ctx->stream>>>(
             s.nw, s.kp / 2, nt, ctx->nv, ctx->nc, ctx->d_Ek.as<double>(),
-            ctx->d_Ekq.as<double>() + (size_t)iq * ctx->nk * ctx->nc, s.w.as<double>(), s.eta, s.wtab.as<float2>());
+            ctx->d_Ekq.as<double>() + (size_t)iq * ctx->nk * ctx->nc, s.w.as<double>(), s.eta, s_a / 32768.0,
+            s.wtab.as<float2>());
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -495,8 +488,8 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     const size_t plane = (size_t)s.ngp * s.kp * 2;
     CUtensorMap mb[NPIECE], ms[NPIECE];
     for (int i = 0; i < NPIECE; ++i)
-        if (!qcx_make_bf16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile) ||
-            !qcx_make_bf16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK))
+        if (!qcx_make_f16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile) ||
+            !qcx_make_f16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK))
             return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute((const void*)k_chi0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

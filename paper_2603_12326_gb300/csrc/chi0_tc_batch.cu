@@ -5,8 +5,9 @@
 // The arithmetic per tile is that of the per-q kernel: one 64-row G' block
 // of one instance at its frequency (a 128 x N accumulator: 64 re rows and 64
 // im rows of chi0_GG'), one N chunk of its G list, the contraction over
-// k' = 2t + p with both operands split into two BF16 terms and the three (or
-// four) split products, FP32 accumulation restarted after 24 MMAs and promoted
+// k' = 2t + p with both operands split into two FP16 terms (pair densities
+// stored as 2^15 rho, W scaled by a power of two) and the three (or four) split
+// products, FP32 accumulation restarted after 24 MMAs and promoted
 // through FP32 registers into an FP64 buffer, and eps = delta - v^1/2 chi0 v^1/2
 // written in FP64 (row G', column G).
 //
@@ -17,7 +18,7 @@
 // memory ring and the two TMEM accumulators keep their phases across tile
 // boundaries, so the TMA producer already streams the next tile while the
 // epilogue warps finish the current one.  Every instance of one q reads the
-// same BF16 planes (the pair densities of the union of that q's G sets,
+// same FP16 planes (the pair densities of the union of that q's G sets,
 // sorted by |q+G| so that each instance's set is a prefix); the planes are
 // addressed through one tensor map per q and piece, all passed by value.  B
 // tiles of N <= 192 rows arrive as 64-row boxes.  Every wait is bounded.
@@ -188,11 +189,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
 #pragma unroll
                         for (int kk = 0; kk < KSTEP / 16; ++kk) {
                             const uint32_t off = kk * 32;
-                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc,
+                            umma_f16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc,
                                       (first && kk == 0) ? 0u : 1u);
-                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
-                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                            if (a.nprod == 4) umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_f16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_f16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                            if (a.nprod == 4) umma_f16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
                         }
                         umma_commit(&empty[s]);
                     }
@@ -293,18 +294,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                                           make_float2(wb.z, wb.w)};
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
-                        const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]);
+                        const float2 f0 = h2f(v0[qq]), f1 = h2f(v1[qq]);
                         const float rr = f0.x + f1.x, ri = f0.y + f1.y;
                         const float2 wq = Wv[qq];
-                        const float xr = wq.x * rr - wq.y * ri;
-                        const float xi = wq.x * ri + wq.y * rr;
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(xr, xi);
-                        const float2 hf = __bfloat1622float2(h);
-                        re0[qq] = *reinterpret_cast<const uint32_t*>(&h);
-                        re1[qq] = pack_bf16(xr - hf.x, xi - hf.y);
+                        split2_h(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq]);
                         // (xi, -xr) splits into the terms of (xr, xi), swapped, the second negated
-                        im0[qq] = __byte_perm(re0[qq], 0u, 0x1032) ^ 0x80000000u;
-                        im1[qq] = __byte_perm(re1[qq], 0u, 0x1032) ^ 0x80000000u;
+                        im0[qq] = perm_im(re0[qq]);
+                        im1[qq] = perm_im(re1[qq]);
                     }
                 }
                 unsigned char* ap = st + NPIECE * BREG + NPIECE * SPIECE;
