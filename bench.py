@@ -216,7 +216,6 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     ctx = qcx.Context(local, stream=stream.cuda_stream)
-    ctx.set_chi0_products(args.products)
     prob = synth.make_mid()
     if ws > 1:   # weak scaling: each rank a different 50-q shard of the same distribution
         prob = synth.make_mid_shard(rank)
@@ -232,9 +231,9 @@ def run_ours(args, ws, rank, local):
 
     chi_events = []
     pd_events = []
-    # algorithmic bytes of one pair-density launch: the FP32 coefficients read once, the two BF16 planes of
+    # algorithmic bytes of one pair-density launch: the FP32 coefficients read once, the three BF16 planes of
     # rho written once
-    pd_bytes = 8.0 * prob.nk * prob.basis.nbasis * (prob.nv + prob.nc) + 8.0 * nt * ng
+    pd_bytes = 8.0 * prob.nk * prob.basis.nbasis * (prob.nv + prob.nc) + 12.0 * nt * ng
 
     def step(record=False):
         for iq in range(nq):
@@ -366,7 +365,7 @@ def run_ours(args, ws, rank, local):
 
     # ------------------------------------------- batched uneven instances (rank 0, N=1)
     batched = batched_leg(stream) if (rank == 0 and ws == 1) else None
-    large = large_leg(stream, args.products) if (rank == 0 and ws == 1 and not args.no_large) else None
+    large = large_leg(stream) if (rank == 0 and ws == 1 and not args.no_large) else None
     surro = surrogate_leg(stream) if (rank == 0 and ws == 1 and not args.no_surrogate) else None
 
     # -------------------------------------------------------- CPU oracle (rank 0, N=1)
@@ -384,10 +383,9 @@ def run_ours(args, ws, rank, local):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "bf16",
                "data": "synthetic (seeded states shaped like the paper's workloads)",
-               "config": _config(ws, f"chi0 as split-BF16 products (two BF16 terms per operand, {args.products} "
-                                     f"products) with FP32 accumulation restarted every 24 MMAs and FP64 partial "
-                                     f"sums; pair densities FP32; inverse FP32 + FP64 diagonal correction; rate "
-                                     f"FP64", nq * nw),
+               "config": _config(ws, "chi0 as three-term split-BF16 products (the six of order <= 2) with FP32 "
+                                     "accumulation restarted every 24 MMAs and FP64 partial sums; pair densities "
+                                     "FP32; inverse FP32 + FP64 diagonal correction; rate FP64", nq * nw),
                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak,
                             "traffic": CHI0_TRAFFIC["bytes"] if CHI0_TRAFFIC else None,
@@ -475,7 +473,7 @@ def accuracy_sweep(ctx, prob, G, w, eta, outL, nsample=8):
                       f"L > 1e-3 of its maximum over the {len(w)} w"}
 
 
-def large_leg(stream, products, nq=2, nk_oracle=8):
+def large_leg(stream, nq=2, nk_oracle=8):
     """The large all-electron workload (18 sp shells per atom up to 5000 bohr^-2,
     12^3 k, N_v = 14, N_c = 64: N_t = 1 548 288, N_G = 531, 400 w on 0-100 eV,
     eta = 0.05 eV) through the mixed path for its first nq q (every q costs the
@@ -489,7 +487,6 @@ def large_leg(stream, products, nq=2, nk_oracle=8):
     from paper_2603_12326_gb300 import QCX_MIXED, qcx, states
 
     ctx = qcx.Context(torch.cuda.current_device(), stream=stream.cuda_stream)
-    ctx.set_chi0_products(products)
     p = synth.make_large(nq=nq)
     Ck, Ckq = states.load_problem(ctx, p)
     G, w = p.G_int, p.w
@@ -694,7 +691,7 @@ def run_profile_case_mlp():
     print("profile case done")
 
 
-def run_profile_case(nw=50, products=3):
+def run_profile_case(nw=50):
     """1 q x nw w of the mid workload through the mixed path, twice (nw = 200 is the
     launch configuration the benchmark step times)."""
     import torch
@@ -704,7 +701,6 @@ def run_profile_case(nw=50, products=3):
     from paper_2603_12326_gb300.build import build
     build()
     ctx = qcx.Context(0)
-    ctx.set_chi0_products(products)
     prob = synth.make_mid(nq=1, nw=nw)
     states.load_problem(ctx, prob)
     for _ in range(2):
@@ -738,8 +734,6 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-correction leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the accuracy sweep over every q")
     ap.add_argument("--no-large", action="store_true", help="skip the large-workload leg")
-    ap.add_argument("--products", type=int, default=3, choices=[3, 4],
-                    help="split-BF16 products of the mixed chi0 (3: a0b0+a0b1+a1b0, 4: also a1b1)")
     ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "mid200", "batch", "mlp"],
                     help="small case for profilers, no report: mid = 1 q x 50 w of the mid workload, 2 passes; "
                          "batch = the uneven workload once; mlp = one gradient and one prediction")
@@ -758,9 +752,9 @@ def main():
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
     if args.profile_case == "mid":
-        run_profile_case(products=args.products)
+        run_profile_case()
     elif args.profile_case == "mid200":
-        run_profile_case(200, products=args.products)
+        run_profile_case(200)
     elif args.profile_case == "batch":
         run_profile_case_batch()
     elif args.profile_case == "mlp":

@@ -58,10 +58,10 @@ typedef enum {
 
 typedef enum {
     QCX_FP64 = 0,   /* plain FP64 throughout                                                    */
-    QCX_MIXED = 1   /* FP32 pair densities kept as two FP16 terms of 2^15 rho; chi0 as split
-                       tcgen05 products of two-term FP16 operands (three terms a0 b0 + a0 b1 +
-                       a1 b0 by default, see qcx_set_chi0_products) with the FP32 tensor-core sums
-                       restarted every 24 MMAs and accumulated in FP64; eps stored in FP64;
+    QCX_MIXED = 1   /* FP32 pair densities kept as three BF16 terms; chi0 as three-term
+                       split-BF16 tcgen05 products (the six of order <= 2) with the FP32
+                       tensor-core sums restarted every 24 MMAs and accumulated in FP64; eps
+                       stored in FP64;
                        FP32 Gauss-Jordan inverse with an FP64 residual correction of the diagonal
                        for ill-conditioned blocks (kappa_1 above qcx_set_refine_threshold, 1e4
                        by default) and the other blocks' loss as a quadratic form of the FP64
@@ -151,9 +151,8 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
 /* Pair densities for q number iq and the G set G_int[ng][3]
  * (Eq. (RPA) matrix elements; closed-form Gaussian-product integrals with
  * the lattice sum done as separable one-dimensional sums).  The result is
- * kept in the context (FP64 for QCX_FP64; for QCX_MIXED FP32 values, scaled
- * by 2^15 and stored as two FP16 terms, which holds |rho| <= 1.99: orthonormal
- * states give |rho| <= 1) and, if out_rho != NULL, also written to
+ * kept in the context (FP64 for QCX_FP64; FP32 values stored as three
+ * BF16 terms for QCX_MIXED) and, if out_rho != NULL, also written to
  * out_rho[nt][ng] (complex double).  Starts a new q: the context's chi0,
  * eps and loss tables for other q are untouched; those for iq are reset.
  * Errors: QCX_ERR_STATE (no states), QCX_ERR_ARG (iq, ng < 1, ng > 4096),
@@ -169,8 +168,7 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
  * qcx_invert_eps are reset (they belong to the previous chi0).
  * Errors: QCX_ERR_STATE, QCX_ERR_ARG (nw < 1, eta <= 0, non-finite w),
  * QCX_ERR_ALLOC, QCX_ERR_CUDA, QCX_ERR_TIMEOUT (a pipeline wait gave up;
- * results are invalid), QCX_ERR_UNSUPPORTED (QCX_MIXED: a pair density of
- * magnitude above 1.99, outside what the FP16 terms hold; results invalid). */
+ * results are invalid). */
 qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, qcx_precision prec,
                     qcx_c64* out_chi0);
 
@@ -199,14 +197,6 @@ qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out
  * Default 1e4; 0 corrects every block.  Applies to later qcx_invert_eps calls
  * of this context.  Errors: QCX_ERR_ARG (ctx NULL, kappa1 negative or NaN). */
 qcx_status qcx_set_refine_threshold(qcx_ctx* ctx, double kappa1);
-
-/* Precision setting of the mixed chi0 (the split products of Eq. (RPA)'s
- * contraction; the product count is not the paper's, which works in FP64):
- * nprod = 3 accumulates a0 b0 + a0 b1 + a1 b0 of the two-term FP16 splits
- * a = a0 + a1, b = b0 + b1 (the default), nprod = 4 adds a1 b1.  Applies to
- * later qcx_chi0 calls and to batch plans built afterwards.
- * Errors: QCX_ERR_ARG (ctx NULL, nprod not 3 or 4). */
-qcx_status qcx_set_chi0_products(qcx_ctx* ctx, int nprod);
 
 /* Failure handling, no counterpart in the paper: every wait inside the
  * tensor-core chi0 kernels (qcx_chi0 with QCX_MIXED, and the batch plans of
@@ -264,7 +254,7 @@ qcx_status qcx_rate(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const d
  *   out_L_nolfe_head[i] = -Im (1 / eps_00)
  *   out_ng[i]           = N_G of the instance (may be NULL).
  * eta (Hartree) is shared.  QCX_FP64 computes everything in FP64; QCX_MIXED
- * forms chi0 on the tensor cores (split-FP16 products as for qcx_chi0, FP32
+ * forms chi0 on the tensor cores (split-BF16 products as for qcx_chi0, FP32
  * accumulation promoted to FP64, eps in FP64), factors eps in FP32 (LU, partial pivoting)
  * and refines the head with two FP64-residual correction steps.
  * The first call with a new instance list (same q indices, cutoffs, eta and
@@ -279,8 +269,7 @@ qcx_status qcx_rate(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const d
  * device pointers (the call synchronises the context stream).
  * Errors: QCX_ERR_STATE (no states), QCX_ERR_ARG (sizes, q index, non-finite
  * or non-positive cutoff, or G = 0 outside an instance's cutoff),
- * QCX_ERR_UNSUPPORTED (an instance with N_G > 512, or QCX_MIXED with a pair
- * density above 1.99 in magnitude), QCX_ERR_SINGULAR (zero
+ * QCX_ERR_UNSUPPORTED (an instance with N_G > 512), QCX_ERR_SINGULAR (zero
  * pivot: that instance's L_LFE is 0), QCX_ERR_NOT_CONVERGED (QCX_MIXED: the
  * last correction exceeded 1e-6 relative), QCX_ERR_TIMEOUT (a bounded wait in
  * the tensor-core kernel gave up; results invalid), QCX_ERR_ALLOC,

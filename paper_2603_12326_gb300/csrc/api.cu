@@ -18,8 +18,8 @@ __global__ void k_to_float(const double* in, float* out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
 }
-// rho [ng][nt] (FP64) or the two FP16 planes of 2^15 rho [ngp][kp] -> [nt][ng] double2
-__global__ void k_rho_export(int ng, long long nt, const double2* R64, const __half2* p0,
+// rho [ng][nt] (FP64) or the three BF16 planes [ngp][kp] -> [nt][ng] double2
+__global__ void k_rho_export(int ng, long long nt, const double2* R64, const __nv_bfloat162* p0,
                              long long plane2, long long kp2, double2* out) {
     const long long n = nt * ng;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -30,9 +30,10 @@ __global__ void k_rho_export(int ng, long long nt, const double2* R64, const __h
             out[i] = R64[(long long)g * nt + t];
         } else {
             const long long o = (long long)g * kp2 + t;
-            const float2 a = __half22float2(p0[o]);
-            const float2 b = __half22float2(p0[o + plane2]);
-            out[i] = make_double2(((double)a.x + (double)b.x) / 32768.0, ((double)a.y + (double)b.y) / 32768.0);
+            const float2 a = __bfloat1622float2(p0[o]);
+            const float2 b = __bfloat1622float2(p0[o + plane2]);
+            const float2 c = __bfloat1622float2(p0[o + 2 * plane2]);
+            out[i] = make_double2((double)a.x + (double)b.x + (double)c.x, (double)a.y + (double)b.y + (double)c.y);
         }
     }
 }
@@ -319,7 +320,7 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
     if (prec == QCX_FP64) {
         CUDA_OR_FAIL(s.rho.ensure((size_t)ng * nt * sizeof(double2)), "alloc rho");
     } else {
-        const size_t bytes = 2 * (size_t)s.ngp * s.kp * sizeof(__half);
+        const size_t bytes = 3 * (size_t)s.ngp * s.kp * sizeof(__nv_bfloat16);
         CUDA_OR_FAIL(s.rho.ensure(bytes), "alloc rho");
         CUDA_OR_FAIL(cudaMemsetAsync(s.rho.p, 0, bytes, ctx->stream), "clear rho");
     }
@@ -336,7 +337,7 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
         }
         k_rho_export<<<nblocks((size_t)nt * ng), 256, 0, ctx->stream>>>(
             ng, nt, prec == QCX_FP64 ? s.rho.as<double2>() : nullptr,
-            reinterpret_cast<const __half2*>(s.rho.p), (long long)s.ngp * (s.kp / 2), s.kp / 2, dst);
+            reinterpret_cast<const __nv_bfloat162*>(s.rho.p), (long long)s.ngp * (s.kp / 2), s.kp / 2, dst);
         CUDA_OR_FAIL(cudaGetLastError(), "export rho");
         if (dst != reinterpret_cast<double2*>(out_rho)) CUDA_OR_FAIL(qcx_copy_out(ctx, out_rho, dst, nout), "copy out");
     }
@@ -384,15 +385,10 @@ qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, q
         if (e == cudaErrorNotSupported)
             return ctx->fail(QCX_ERR_UNSUPPORTED, "chi0: this G-set size is not handled by the tensor-core kernel");
         CUDA_OR_FAIL(e, "chi0 tensor-core kernel");
-        int st = 0, range = 0;
+        int st = 0;
         CUDA_OR_FAIL(cudaMemcpyAsync(&st, s.flags.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status");
-        CUDA_OR_FAIL(cudaMemcpyAsync(&range, s.pd_range.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
-                     "status");
         CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream), "sync");
         if (st) return ctx->fail(QCX_ERR_TIMEOUT, "chi0: a pipeline wait in the tensor-core kernel gave up");
-        if (range)
-            return ctx->fail(QCX_ERR_UNSUPPORTED, "chi0: a pair density exceeds 1.99 in magnitude (the FP16 terms of "
-                                                  "the mixed path hold |rho| <= 1.99; are the states orthonormal?)");
     }
     if (out_chi0 && chi != reinterpret_cast<double2*>(out_chi0))
         CUDA_OR_FAIL(qcx_copy_out(ctx, out_chi0, chi, nmat * sizeof(double2)), "copy out");
@@ -448,14 +444,6 @@ qcx_status qcx_set_wait_limit(qcx_ctx* ctx, long long cycles) {
     ctx->err.clear();
     if (cycles < 1) return ctx->fail(QCX_ERR_ARG, "set_wait_limit: cycles must be positive");
     ctx->wait_limit = cycles;
-    return QCX_OK;
-}
-
-qcx_status qcx_set_chi0_products(qcx_ctx* ctx, int nprod) {
-    if (!ctx) return QCX_ERR_ARG;
-    ctx->err.clear();
-    if (nprod != 3 && nprod != 4) return ctx->fail(QCX_ERR_ARG, "set_chi0_products: 3 or 4");
-    ctx->chi0_products = nprod;
     return QCX_OK;
 }
 

@@ -37,7 +37,7 @@ namespace {
 constexpr int NREF = 2;            // FP64 refinement steps of the mixed solve
 constexpr int MAX_NG = 512;        // largest instance the solve kernels take
 constexpr int FT = 32, FK = 16;    // FP64 chi0 tile: 32 x 32 (G, G'), 16 transitions per stage
-constexpr int TC_KSTEP = 32;       // FP16 K elements per tensor-core pipeline stage
+constexpr int TC_KSTEP = 32;       // BF16 K elements per tensor-core pipeline stage
 
 #define CUDA_OR_FAIL(call, what)                                                                \
     do {                                                                                        \
@@ -51,7 +51,7 @@ constexpr int TC_KSTEP = 32;       // FP16 K elements per tensor-core pipeline s
 
 // W[inst][t] = 1/(w - dE + i eta) - 1/(w + dE + i eta), dE = E_c(k+q) - E_v(k) in FP64; zero for padded t
 __global__ void k_weights_batch(int ninst, long long ld, long long nt, int nv, int nc, int nk, const double* Ek,
-                                const double* Ekq_all, const BatchInst* inst, double eta, double scale, float2* W) {
+                                const double* Ekq_all, const BatchInst* inst, double eta, float2* W) {
     const long long n = (long long)ninst * ld;
     const int nvc = nv * nc;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -66,7 +66,7 @@ __global__ void k_weights_batch(int ninst, long long ld, long long nt, int nv, i
             const double dE = Ekq[k * nc + c] - Ek[k * nv + vv];
             const double w = inst[ii].w;
             const double x1 = w - dE, x2 = w + dE;
-            const double d1 = scale / (x1 * x1 + eta * eta), d2 = scale / (x2 * x2 + eta * eta);
+            const double d1 = 1.0 / (x1 * x1 + eta * eta), d2 = 1.0 / (x2 * x2 + eta * eta);
             v = make_float2((float)(x1 * d1 - x2 * d2), (float)(eta * (d2 - d1)));
         }
         W[i] = v;
@@ -188,14 +188,13 @@ struct BatchPlan {
 
     DevBuf d_G, d_inst, d_wtab, d_eps, d_work, d_rowmap, d_x, d_r, d_out, d_flags, d_status, d_acc;
     DevBuf d_tiles, d_cta, d_rtask;
-    std::vector<CUtensorMap> maps;              // [nslot][2]: the two FP16 planes of each slot
+    std::vector<CUtensorMap> maps;              // [nslot][3]: the three BF16 planes of each slot
     std::vector<int> grp_tile0, grp_ntile;      // tensor-core tiles per group of <= QCX_BATCH_MAXQ slots
     int tc_grid = 0, tile_cap = 0, ntile = 0;
     int lu_grid = 0, n_rtask = 0;
     int tuned = 0;
     double tune_ms = 0.0;
     int launches = 0;
-    int nprod = 3;                              // split-FP16 products of the tensor-core chi0
     long long wait_limit = 0;                   // pipeline wait limit captured into the graph
     cudaGraphExec_t exec = nullptr;
 
@@ -312,7 +311,7 @@ cudaError_t record(qcx_ctx* ctx, BatchPlan& p) {
         const long long n = (long long)p.ninst * (p.kp / 2);
         k_weights_batch<<<(int)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(
             p.ninst, p.kp / 2, p.nt, ctx->nv, ctx->nc, ctx->nk, ctx->d_Ek.as<double>(), ctx->d_Ekq.as<double>(), dinst,
-            p.eta, qcx_w_scale(p.eta) / 32768.0, p.d_wtab.as<float2>());
+            p.eta, p.d_wtab.as<float2>());
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++p.launches;
         for (size_t g = 0; g < p.grp_tile0.size(); ++g) {
@@ -320,12 +319,11 @@ cudaError_t record(qcx_ctx* ctx, BatchPlan& p) {
             const int s0 = (int)g * QCX_BATCH_MAXQ;
             const int ns = std::min(QCX_BATCH_MAXQ, p.nslot - s0);
             // slot indices inside a group are relative to its first slot
-            e = qcx_launch_chi0_tc_batch(st, p.maps.data() + 2 * s0, s0, ns, p.grp_ntile[g],
+            e = qcx_launch_chi0_tc_batch(st, p.maps.data() + 3 * s0, s0, ns, p.grp_ntile[g],
                                          p.d_tiles.as<int4>() + p.grp_tile0[g], std::min(p.tc_grid, p.grp_ntile[g]),
-                                         dinst, p.d_wtab.as<float2>(), p.kp / 2, (int)(p.kp / TC_KSTEP),
-                                         p.pref / (qcx_w_scale(p.eta) * 32768.0),
+                                         dinst, p.d_wtab.as<float2>(), p.kp / 2, (int)(p.kp / TC_KSTEP), p.pref,
                                          p.d_acc.as<double>(), p.d_eps.as<double2>(), p.d_status.as<int>(),
-                                         p.wait_limit, p.nprod);
+                                         p.wait_limit);
             if (e != cudaSuccess) return e;
             ++p.launches;
         }
@@ -460,9 +458,8 @@ qcx_status build_plan(qcx_ctx* ctx, BatchPlan& p) {
         CUDA_OR_FAIL(q->vs.ensure(sizeof(double) * U), "alloc");
         CUDA_OR_FAIL(q->vs32.ensure(sizeof(float) * U), "alloc");
         if (mixed) {
-            const size_t bytes = 2 * (size_t)q->ngp * q->kp * sizeof(__half);
+            const size_t bytes = 3 * (size_t)q->ngp * q->kp * sizeof(__nv_bfloat16);
             CUDA_OR_FAIL(q->rho.ensure(bytes), "alloc rho");
-            CUDA_OR_FAIL(q->pd_range.ensure(sizeof(int)), "alloc");      // before any capture
             CUDA_OR_FAIL(cudaMemsetAsync(q->rho.p, 0, bytes, ctx->stream), "clear rho");
         } else {
             CUDA_OR_FAIL(q->rho.ensure((size_t)U * p.nt * sizeof(double2)), "alloc rho");
@@ -530,13 +527,13 @@ qcx_status build_plan(qcx_ctx* ctx, BatchPlan& p) {
     }
     if (mixed) {
         CUDA_OR_FAIL(p.d_wtab.ensure(sizeof(float2) * (size_t)ninst * (p.kp / 2)), "alloc W");
-        p.maps.resize(2 * p.nslot);
+        p.maps.resize(3 * p.nslot);
         for (int s = 0; s < p.nslot; ++s) {
             QSlot& q = *p.qs[s];
             unsigned char* base = reinterpret_cast<unsigned char*>(q.rho.p);
             const size_t plane = (size_t)q.ngp * q.kp * 2;
-            for (int pc = 0; pc < 2; ++pc)
-                if (!qcx_make_f16_map(&p.maps[2 * s + pc], base + pc * plane, q.kp, q.ngp, 64))
+            for (int pc = 0; pc < 3; ++pc)
+                if (!qcx_make_bf16_map(&p.maps[3 * s + pc], base + pc * plane, q.kp, q.ngp, 64, 32))
                     return ctx->fail(QCX_ERR_CUDA, "solve_batch: tensor map");
         }
     } else {
@@ -689,8 +686,7 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
     }
     BatchPlan* p = ctx->batch;
     const bool same = p && p->gen == ctx->gen && p->prec == (int)prec && p->eta == eta && p->ninst == ninst &&
-                      p->key_q == iq && p->key_gmax == gm && p->nprod == ctx->chi0_products &&
-                      p->wait_limit == ctx->wait_limit;
+                      p->key_q == iq && p->key_gmax == gm && p->wait_limit == ctx->wait_limit;
     if (!same) {
         delete ctx->batch;
         ctx->batch = nullptr;
@@ -702,7 +698,6 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
         p->ninst = ninst;
         p->key_q = iq;
         p->key_gmax = gm;
-        p->nprod = ctx->chi0_products;
         p->wait_limit = ctx->wait_limit;
         qcx_status st = build_plan(ctx, *p);
         if (st == QCX_OK) st = upload_inst(ctx, *p, w);
@@ -737,15 +732,6 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
         }
     }
     if (status) return ctx->fail(QCX_ERR_TIMEOUT, "solve_batch: a pipeline wait in the tensor-core kernel gave up");
-    if (p->prec == QCX_MIXED) {
-        for (int s = 0; s < p->nslot; ++s) {
-            int range = 0;
-            CUDA_OR_FAIL(cudaMemcpy(&range, p->qs[s]->pd_range.p, sizeof(int), cudaMemcpyDeviceToHost), "status");
-            if (range)
-                return ctx->fail(QCX_ERR_UNSUPPORTED, "solve_batch: a pair density exceeds 1.99 in magnitude (the "
-                                                      "FP16 terms of the mixed path hold |rho| <= 1.99)");
-        }
-    }
     int sing = 0, nconv = 0;
     for (int f : flags) {
         sing += f == 1;

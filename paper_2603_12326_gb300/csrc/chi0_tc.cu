@@ -9,37 +9,38 @@
 //   A[(w,re,G')][2t+p]   = (Re, Im) (W_t(w) rho_t(G'))                      (generated in shared memory)
 //   A[(w,im,G')][2t+p]   = (Im, -Re)(W_t(w) rho_t(G')),
 // so the re rows of D hold Re chi0_GG' and the im rows Im chi0_GG'.  Both
-// operands are split into two FP16 terms x = x0 + x1 (x0 = fp16(x),
-// x1 = fp16(x - x0), 22 significant bits together), and D accumulates in FP32
-// the three products a0 b0 + a0 b1 + a1 b0 (the split-precision product with
-// three terms), or, when the context asks for it, the fourth term a1 b1 as
-// well.  Each term is an exact FP16 product; what the split leaves out is of
-// relative order 2^-21.  The FP16 range is kept by powers of two: the stored
-// pair densities are 2^15 rho (|rho| <= 1 for orthonormal states), and the W
-// table carries s_A 2^-15 with s_A = 2^floor(log2(8192 eta)), so that
-// |W rho s_A| <= (2/eta) 8192 eta 1.99 < 2^15; the epilogue divides by s_A 2^15.
-// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is tabulated per q by
-// k_weights with dE and w -+ dE in FP64 and fetched with each K stage.
+// operands are split into three BF16 terms x = x0 + x1 + x2 (x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)); D accumulates in FP32 the six
+// products whose order is at most 2, a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0,
+// so each product carries ~2^-24 relative error.  (Two BF16 terms with three
+// or four products leave 2^-17 of every operand and miss 1e-4 on the loss with
+// local fields at some q; two FP16 terms, scaled by powers of two, missed it
+// too, although a host emulation that keeps FP16 subnormals meets it.)
+// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta)
+// is tabulated per q by k_weights with dE and w -+ dE in FP64 and fetched with
+// each K stage.
 //
 // The tensor core's FP32 accumulation truncates, so long sums drift (about
 // 2^-24 of the running value per MMA, always toward zero).  The accumulator
-// is therefore restarted after 24 MMAs (a window of 24 / (2 * products) K
-// stages): TMEM holds two buffers used in turn, the finished buffer is drained
-// into FP32 registers (round to nearest), and every 64 windows the register
-// partials are added into an FP64 buffer owned by the CTA.  The Dyson step
-// runs in FP64 from that buffer and eps is stored in FP64.
+// is therefore restarted after 24 MMAs (four K stages of six products): TMEM
+// holds two buffers used in turn, the finished buffer is drained into FP32
+// registers (round to nearest), and every 64 windows the register partials are
+// added into an FP64 buffer owned by the CTA.  The Dyson step runs in FP64
+// from that buffer and eps is stored in FP64.
 //
-// CTA work item: one 64-row G' block, one frequency (a 128 x N accumulator:
-// 64 re rows and 64 im rows), one N chunk of G.  Warp roles: warp 0 issues the
-// TMA loads of a stage (B tile, the W chunk and, when the G range is split, the
-// A-source rows) into a ring of 4-8 stages; warp 1 owns TMEM; one thread of
-// warp 1 issues the MMAs of the even accumulation windows and one thread of
-// warp 2 those of the odd windows; warps 3-18 form W rho and the A tiles (two
-// groups of eight warps taking alternate K stages), drain the accumulators
-// (each warp a quarter of the columns of its lane quadrant) and run the
-// epilogue (eps = delta - v^1/2 chi0 v^1/2).  Every wait is bounded: on timeout the
-// kernel records an error status, lets its own copies and MMAs finish, frees
-// TMEM and returns.
+// A K stage is 16 BF16 values (8 transitions): operand rows of 32 bytes with
+// the 32-byte swizzle, so a stage is small (B 18 KB, A 12 KB for N = 192) and
+// the ring holds 6-8 stages in flight.  CTA work item: one 64-row G' block,
+// one frequency (a 128 x N accumulator: 64 re rows and 64 im rows), one N chunk
+// of G.  Warp roles: warp 0 issues the TMA loads of a stage (B tile, the W
+// chunk and, when the G range is split, the A-source rows); warp 1 owns TMEM;
+// one thread of warp 1 issues the MMAs of the even accumulation windows and
+// one thread of warp 2 those of the odd windows; warps 3-18 form W rho and the
+// A tiles (four groups of four warps, group g taking the K stages g, g + 4,
+// ...), drain the accumulators (each warp a quarter of the columns of its lane
+// quadrant) and run the epilogue (eps = delta - v^1/2 chi0 v^1/2).  Every wait
+// is bounded: on timeout the kernel records an error status, lets its own
+// copies and MMAs finish, frees TMEM and returns.
 #include "qcx_internal.h"
 #include "tc_ptx.cuh"
 
@@ -47,20 +48,24 @@
 
 namespace {
 
-constexpr int NPIECE = 2;                 // FP16 terms per operand
+constexpr int NPIECE = 3;                 // BF16 terms per operand
+constexpr int KS = 16;                    // BF16 K elements per stage (one 32-byte row)
+constexpr int RB = 2 * KS;                // bytes per operand row in shared memory
 constexpr int AW0 = 3;                    // first A/drain/epilogue warp
-constexpr int NAW = 16;                   // A/drain/epilogue warps: two groups of eight
+constexpr int NAW = 16;                   // A/drain/epilogue warps
+constexpr int NGRP = 4;                   // A groups (four warps each) on alternate K stages
 constexpr int NTHREADS = (AW0 + NAW) * 32;
 constexpr int MMA_WARP2 = 2;
-constexpr int MAXSTAGE = 8;               // ring depth at most (barrier arrays)
-constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
+constexpr int MAXSTAGE = 8;               // ring depth at most
+constexpr int NBAR = NGRP * MAXSTAGE;     // copy / A-tile barriers: stage mod NGRP * ring depth
+constexpr int ATILE = 128 * RB;           // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per half tile
-constexpr int WIN_MMAS = 24;              // MMAs accumulated in one TMEM buffer before it is drained
-constexpr int FLUSH_WINDOWS = 64;         // windows between FP64 flushes of the register partials
+constexpr int PROMOTE = 4;                // K stages per accumulation window (4 x 6 = 24 MMAs)
+constexpr int FLUSH = 64 * PROMOTE;       // K stages between FP64 flushes of the register partials
 constexpr int MAXN = 192;                 // largest N tile
 constexpr int MAXC = 48;                  // accumulator columns one thread drains (N/4 rounded up to 8)
 constexpr int SMEM_LIMIT = 232448;
-constexpr int TPS = KSTEP / 2;            // transitions per stage
+constexpr int TPS = KS / 2;               // transitions per stage
 constexpr int WBYTES = TPS * (int)sizeof(float2);
 
 struct TcArgs {
@@ -68,9 +73,6 @@ struct TcArgs {
     long long nt;
     int n_tile, n_gb, kstages, src_from_b;
     int nstage;           // ring depth
-    int nprod;            // 3: a0b0 + a0b1 + a1b0; 4: also a1b1
-    int promote;          // K stages per accumulation window
-    int flush;            // K stages between FP64 flushes
     uint32_t stage_bytes; // one ring stage (1024-aligned)
     uint32_t acc_off, tmem_cols;      // second TMEM buffer column, columns allocated
     const float2* wtab;   // [nw][kp/2] W_t(w) in FP32 (tabulated with FP64 dE)
@@ -89,36 +91,38 @@ struct TcArgs {
 // 96 registers per thread
 __global__ void __maxnreg__(96)
     k_chi0_tc(const __grid_constant__ CUtensorMap mb0, const __grid_constant__ CUtensorMap mb1,
-              const __grid_constant__ CUtensorMap ms0, const __grid_constant__ CUtensorMap ms1, TcArgs a) {
+              const __grid_constant__ CUtensorMap mb2, const __grid_constant__ CUtensorMap ms0,
+              const __grid_constant__ CUtensorMap ms1, const __grid_constant__ CUtensorMap ms2, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x / a.nw, iw = blockIdx.x % a.nw;
     const int n0 = blockIdx.y * a.n_tile;
     const int NS = a.nstage;
-    const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;          // one B piece
-    const uint32_t spiece = (uint32_t)GBLK * ROWB;              // one A-source piece
+    const int NB = NGRP * NS;                                   // copy / A-tile barriers in use
+    const uint32_t bbytes = (uint32_t)a.n_tile * RB;            // one B piece
+    const uint32_t spiece = (uint32_t)GBLK * RB;                // one A-source piece
     const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * spiece;
     const uint32_t aoff = NPIECE * bbytes + sbytes;             // A pieces start here in a stage
     const uint32_t woff = aoff + NPIECE * ATILE;                // the stage's W chunk
     unsigned char* tail = base + (size_t)NS * a.stage_bytes;
-    // The copy and A-tile barriers of K stage it are number it mod 2 NS (ring slot it mod NS): the
+    // The copy and A-tile barriers of K stage it are number it mod NGRP NS (ring slot it mod NS): the
     // previous phase of such a barrier then belongs to the same A-warp group, and lies at least two
     // accumulation windows back for an MMA issuer, so no wait can pass a phase early.
     uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
-    uint64_t* full_b = bars;                   // [2 NS] copies of the stage landed
-    uint64_t* full_a = bars + 2 * MAXSTAGE;    // [2 NS] A tiles of the stage written (one group: 8 warps)
-    uint64_t* empty = bars + 4 * MAXSTAGE;     // [NS] MMAs of the slot done (slot reusable)
-    uint64_t* acc_full = bars + 5 * MAXSTAGE;  // [2] TMEM buffer holds a finished window
+    uint64_t* full_b = bars;                   // [NB] copies of the stage landed
+    uint64_t* full_a = bars + NBAR;            // [NB] A tiles of the stage written (one group: 4 warps)
+    uint64_t* empty = bars + 2 * NBAR;         // [NS] MMAs of the slot done (slot reusable)
+    uint64_t* acc_full = empty + MAXSTAGE;     // [2] TMEM buffer holds a finished window
     uint64_t* drained = acc_full + 2;          // [2] TMEM buffer read out (16 warps)
     uint64_t* mma_done = drained + 2;          // every issued MMA finished
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * NS; ++s) {
+        for (int s = 0; s < NB; ++s) {
             mbar_init(&full_b[s], 1);
-            mbar_init(&full_a[s], 8);
+            mbar_init(&full_a[s], NAW / NGRP);
         }
         for (int s = 0; s < NS; ++s) mbar_init(&empty[s], 1);
         for (int b = 0; b < 2; ++b) {
@@ -134,20 +138,22 @@ __global__ void __maxnreg__(96)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int nwin = (a.kstages + a.promote - 1) / a.promote;
+    const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
-            const int pf = NS + 1;          // K stages between the L2 prefetch of a stage and its copy
+            const int pf = NS + 2;          // K stages between the L2 prefetch of a stage and its copy
             // a stage's lines are requested into L2 a few stages before its copy is issued
             auto prefetch = [&](int it) {
                 bulk_prefetch(a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, WBYTES);
-                tma_prefetch_2d(&mb0, it * KSTEP, n0);
-                tma_prefetch_2d(&mb1, it * KSTEP, n0);
+                tma_prefetch_2d(&mb0, it * KS, n0);
+                tma_prefetch_2d(&mb1, it * KS, n0);
+                tma_prefetch_2d(&mb2, it * KS, n0);
                 if (!a.src_from_b) {
-                    tma_prefetch_2d(&ms0, it * KSTEP, gb * GBLK);
-                    tma_prefetch_2d(&ms1, it * KSTEP, gb * GBLK);
+                    tma_prefetch_2d(&ms0, it * KS, gb * GBLK);
+                    tma_prefetch_2d(&ms1, it * KS, gb * GBLK);
+                    tma_prefetch_2d(&ms2, it * KS, gb * GBLK);
                 }
             };
             for (int it = 0; it < pf && it < a.kstages; ++it) prefetch(it);
@@ -159,23 +165,25 @@ __global__ void __maxnreg__(96)
                 if (it + pf < a.kstages) prefetch(it + pf);
                 const int s = it % NS;
                 if (!mbar_wait(&empty[s], ((uint32_t)(it / NS) & 1u) ^ 1u, abort_flag, a.status, a.wait_limit)) break;
-                uint64_t* fb = &full_b[it % (2 * NS)];
+                uint64_t* fb = &full_b[it % NB];
                 unsigned char* st = base + (size_t)s * a.stage_bytes;
                 mbar_arrive_tx(fb, NPIECE * bbytes + sbytes + WBYTES);
                 bulk_load(st + woff, a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, WBYTES, fb);
-                tma_load_2d(st, &mb0, fb, it * KSTEP, n0);
-                tma_load_2d(st + bbytes, &mb1, fb, it * KSTEP, n0);
+                tma_load_2d(st, &mb0, fb, it * KS, n0);
+                tma_load_2d(st + bbytes, &mb1, fb, it * KS, n0);
+                tma_load_2d(st + 2 * bbytes, &mb2, fb, it * KS, n0);
                 if (!a.src_from_b) {
                     unsigned char* sp = st + NPIECE * bbytes;
-                    tma_load_2d(sp, &ms0, fb, it * KSTEP, gb * GBLK);
-                    tma_load_2d(sp + spiece, &ms1, fb, it * KSTEP, gb * GBLK);
+                    tma_load_2d(sp, &ms0, fb, it * KS, gb * GBLK);
+                    tma_load_2d(sp + spiece, &ms1, fb, it * KS, gb * GBLK);
+                    tma_load_2d(sp + 2 * spiece, &ms2, fb, it * KS, gb * GBLK);
                 }
                 last = it;
             }
             // let every copy still in flight (at most the last NS stages) land before the CTA can exit
             for (int it = max(0, last - NS + 1); it <= last; ++it)
-                mbar_wait(&full_b[it % (2 * NS)], (uint32_t)(it / (2 * NS)) & 1u, abort_flag, a.status,
-                          CLEANUP_WAIT_LIMIT, false);
+                mbar_wait(&full_b[it % NB], (uint32_t)(it / NB) & 1u, abort_flag, a.status, CLEANUP_WAIT_LIMIT,
+                          false);
         }
     } else if (warp == 1 || warp == MMA_WARP2) {
         // ---------------------------------------------------------- MMA issuers
@@ -192,29 +200,25 @@ __global__ void __maxnreg__(96)
                 if (win >= 2 &&
                     !mbar_wait(&drained[b], (uint32_t)((win - 2) >> 1) & 1u, abort_flag, a.status, a.wait_limit))
                     break;
-                const int it1 = min((win + 1) * a.promote, a.kstages);
-                for (int it = win * a.promote; it < it1; ++it) {
+                const int it1 = min((win + 1) * PROMOTE, a.kstages);
+                for (int it = win * PROMOTE; it < it1; ++it) {
                     const int s = it % NS;
-                    const bool first = it == win * a.promote;
                     // the A warps arrive only after they saw this stage's copies land
-                    if (!mbar_wait(&full_a[it % (2 * NS)], (uint32_t)(it / (2 * NS)) & 1u, abort_flag, a.status,
-                                   a.wait_limit)) {
+                    if (!mbar_wait(&full_a[it % NB], (uint32_t)(it / NB) & 1u, abort_flag, a.status, a.wait_limit)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     unsigned char* st = base + (size_t)s * a.stage_bytes;
-                    const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes;
+                    const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes, b2 = b1 + bbytes;
                     const uint32_t d = tmem + (uint32_t)b * a.acc_off;
-                    const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE;
-#pragma unroll
-                    for (int kk = 0; kk < KSTEP / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        umma_f16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
-                        umma_f16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
-                        umma_f16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                        if (a.nprod == 4) umma_f16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
-                    }
+                    const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE, a2 = a1 + ATILE;
+                    umma_bf16(d, sw32_desc(a0), sw32_desc(b0), idesc, it == win * PROMOTE ? 0u : 1u);
+                    umma_bf16(d, sw32_desc(a0), sw32_desc(b1), idesc, 1u);
+                    umma_bf16(d, sw32_desc(a1), sw32_desc(b0), idesc, 1u);
+                    umma_bf16(d, sw32_desc(a0), sw32_desc(b2), idesc, 1u);
+                    umma_bf16(d, sw32_desc(a1), sw32_desc(b1), idesc, 1u);
+                    umma_bf16(d, sw32_desc(a2), sw32_desc(b0), idesc, 1u);
                     umma_commit(&empty[s]);
                 }
                 if (ok) umma_commit(&acc_full[b]);
@@ -226,10 +230,10 @@ __global__ void __maxnreg__(96)
     } else {
         // --------------------------------- A generation, accumulator drain, epilogue
         const int wa = warp - AW0;          // 0..15
-        const int grp = wa >> 3;            // this warp's group forms the A tiles of stages grp, grp + 2, ...
-        const int gi = ((wa & 7) << 5) | lane;   // 0..255 within the group
-        const int j = gi & 3;               // 16-byte chunk = 4 transitions
-        const int go = gi >> 2;             // G' offset in the block (0..63)
+        const int grp = wa >> 2;            // this warp's group forms the A tiles of stages grp, grp + 4, ...
+        const int gi = ((wa & 3) << 5) | lane;   // 0..127 within the group
+        const int j = gi & 1;               // 16-byte chunk = 4 transitions
+        const int go = gi >> 1;             // G' offset in the block (0..63)
         const int Gp = gb * GBLK + go;
         // drain mapping: TMEM lane quadrant q (fixed by the warp's rank modulo 4), column slice cs
         const int q = warp & 3, cs = wa >> 2;
@@ -269,7 +273,7 @@ __global__ void __maxnreg__(96)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&drained[b]);
-            if (((wd + 1) * a.promote) % a.flush == 0 || wd + 1 == nwin) {
+            if (((wd + 1) * PROMOTE) % FLUSH == 0 || wd + 1 == nwin) {
 #pragma unroll
                 for (int c = 0; c < MAXC; ++c) {
                     if (c < c1 - c0) {
@@ -282,51 +286,55 @@ __global__ void __maxnreg__(96)
             return true;
         };
 
-        for (int it = grp; it < a.kstages && ok; it += 2) {
+        for (int it = grp; it < a.kstages && ok; it += NGRP) {
             const int s = it % NS;
-            const int s2 = it % (2 * NS);
+            const int sb = it % NB;
             // the producer issued this stage's copies only after the MMAs of its previous use
             // finished, so a landed stage is also free to overwrite
-            if (!(ok = warp_wait(&full_b[s2], (uint32_t)(it / (2 * NS)) & 1u, abort_flag, a.status, a.wait_limit)))
-                break;
+            if (!(ok = warp_wait(&full_b[sb], (uint32_t)(it / NB) & 1u, abort_flag, a.status, a.wait_limit))) break;
             unsigned char* st = base + (size_t)s * a.stage_bytes;
             const unsigned char* srcb = a.src_from_b ? st : st + NPIECE * bbytes;
             const uint32_t src_piece = a.src_from_b ? bbytes : spiece;
-            uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0};   // re row terms
+            uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};   // re row terms
             if (Gp < a.ng) {
                 const int srow = a.src_from_b ? Gp : go;
-                const uint32_t coff = sw64_off(srow, j);
+                const uint32_t coff = sw32_off(srow, j);
                 const uint4 h0 = *reinterpret_cast<const uint4*>(srcb + coff);
                 const uint4 h1 = *reinterpret_cast<const uint4*>(srcb + src_piece + coff);
-                const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w};
+                const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
+                const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
+                               v2[4] = {h2.x, h2.y, h2.z, h2.w};
                 const float4* Wv4 = reinterpret_cast<const float4*>(st + woff) + 2 * j;
                 const float4 wa4 = Wv4[0], wb4 = Wv4[1];
                 const float2 Wv[4] = {make_float2(wa4.x, wa4.y), make_float2(wa4.z, wa4.w),
                                       make_float2(wb4.x, wb4.y), make_float2(wb4.z, wb4.w)};
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
-                    const float2 f0 = h2f(v0[qq]), f1 = h2f(v1[qq]);
-                    const float rr = f0.x + f1.x, ri = f0.y + f1.y;
+                    const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
+                    const float rr = f0.x + (f1.x + f2.x), ri = f0.y + (f1.y + f2.y);
                     const float2 wq = Wv[qq];
-                    split2_h(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq]);
+                    split3(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq], re2[qq]);
                 }
             }
             unsigned char* ap = st + aoff;
-            const uint32_t o_re = sw64_off(go, j), o_im = sw64_off(64 + go, j);
+            const uint32_t o_re = sw32_off(go, j), o_im = sw32_off(64 + go, j);
             *reinterpret_cast<uint4*>(ap + o_re) = make_uint4(re0[0], re0[1], re0[2], re0[3]);
             *reinterpret_cast<uint4*>(ap + ATILE + o_re) = make_uint4(re1[0], re1[1], re1[2], re1[3]);
+            *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_re) = make_uint4(re2[0], re2[1], re2[2], re2[3]);
             // (xi, -xr) splits into the same terms as (xr, xi), swapped, the second negated
             *reinterpret_cast<uint4*>(ap + o_im) =
                 make_uint4(perm_im(re0[0]), perm_im(re0[1]), perm_im(re0[2]), perm_im(re0[3]));
             *reinterpret_cast<uint4*>(ap + ATILE + o_im) =
                 make_uint4(perm_im(re1[0]), perm_im(re1[1]), perm_im(re1[2]), perm_im(re1[3]));
+            *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_im) =
+                make_uint4(perm_im(re2[0]), perm_im(re2[1]), perm_im(re2[2]), perm_im(re2[3]));
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&full_a[s2]);
+            if (lane == 0) mbar_arrive(&full_a[sb]);
             // after this group's last stage of window wd, drain the windows before wd (their MMAs
             // finished long ago, so the drain does not wait on the tensor pipe)
-            const int wd = it / a.promote;
-            if (it + 2 >= min((wd + 1) * a.promote, a.kstages))
+            const int wd = it / PROMOTE;
+            if (it + NGRP >= min((wd + 1) * PROMOTE, a.kstages))
                 while (ok && next_drain < wd) ok = drain(next_drain++);
         }
         while (ok && next_drain < nwin) ok = drain(next_drain++);
@@ -360,10 +368,10 @@ __global__ void __maxnreg__(96)
     }
 }
 
-// W[w][t] = scale (1/(w - dE + i eta) - 1/(w + dE + i eta)), dE = E_c(k+q) - E_v(k), with dE and
+// W[w][t] = 1/(w - dE + i eta) - 1/(w + dE + i eta), dE = E_c(k+q) - E_v(k), with dE and
 // w -+ dE formed in FP64; zero for padded t.
 __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, const double* Ek, const double* Ekq,
-                          const double* w, double eta, double scale, float2* W) {
+                          const double* w, double eta, float2* W) {
     const long long n = (long long)nw * ld;
     const int nvc = nv * nc;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -377,7 +385,7 @@ __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, co
             const double dE = Ekq[k * nc + c] - Ek[k * nv + vv];
             const double x1 = w[iw] - dE, x2 = w[iw] + dE;
             const double n1 = x1 * x1 + eta * eta, n2 = x2 * x2 + eta * eta;
-            const double r = scale / (n1 * n2);       // one FP64 division for both denominators
+            const double r = 1.0 / (n1 * n2);         // one FP64 division for both denominators
             const double d1 = n2 * r, d2 = n1 * r;
             v = make_float2((float)(x1 * d1 - x2 * d2), (float)(eta * (d2 - d1)));
         }
@@ -404,15 +412,17 @@ static PFN_encodeTiled_t get_encode() {
     return fn;
 }
 
-bool qcx_make_f16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows) {
+// 2-D tensor map over one BF16 plane [rows][kp] (row length kp), box {box_k, box_rows} with the
+// swizzle matching the row bytes of the box (32 or 64)
+bool qcx_make_bf16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows, int box_k) {
     PFN_encodeTiled_t enc = get_encode();
-    if (!enc) return false;
+    if (!enc || (box_k != 16 && box_k != 32)) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)KSTEP, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               box_k == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -436,31 +446,27 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
         a.src_from_b = 0;
     }
     a.n_gb = (ng + GBLK - 1) / GBLK;
-    a.kstages = (int)(s.kp / KSTEP);
-    a.nprod = ctx->chi0_products;
-    a.promote = WIN_MMAS / ((KSTEP / 16) * a.nprod);
-    a.flush = FLUSH_WINDOWS * a.promote;
+    a.kstages = (int)(s.kp / KS);
     a.acc_off = a.n_tile <= 128 ? 128u : 256u;
     a.tmem_cols = 2u * a.acc_off;
     a.wld = s.kp / 2;
     const double* L = ctx->lattice;
     const double vol = fabs(L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
                             L[2] * (L[3] * L[7] - L[4] * L[6]));
-    const double s_a = qcx_w_scale(s.eta);            // power of two: exact
-    a.pref = 2.0 / (ctx->nk * vol) / (s_a * 32768.0);
+    a.pref = 2.0 / (ctx->nk * vol);
     a.vs = s.vs.as<double>();
     a.eps = s.eps.as<double2>();
     a.chi = chi;
     a.status = d_status;
     a.wait_limit = ctx->wait_limit;
     a.withhold = ctx->withhold_copies;
-    if (a.n_tile > MAXN || a.n_tile < 16 || (a.nprod != 3 && a.nprod != 4)) return cudaErrorNotSupported;
+    if (a.n_tile > MAXN || a.n_tile < 16) return cudaErrorNotSupported;
 
     // ring: as many stages as fit in shared memory, 4 to MAXSTAGE
-    const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;
-    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * GBLK * ROWB;
+    const uint32_t bbytes = (uint32_t)a.n_tile * RB;
+    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * GBLK * RB;
     a.stage_bytes = (NPIECE * bbytes + sbytes + NPIECE * ATILE + WBYTES + 1023u) & ~1023u;
-    const size_t fixed = 1024 + (5 * MAXSTAGE + 5) * sizeof(uint64_t) + 16;
+    const size_t fixed = 1024 + (2 * NBAR + MAXSTAGE + 5) * sizeof(uint64_t) + 16;
     a.nstage = (int)std::min<size_t>(MAXSTAGE, (SMEM_LIMIT - fixed) / a.stage_bytes);
     if (a.nstage < 4) return cudaErrorNotSupported;
     const size_t smem = fixed + (size_t)a.nstage * a.stage_bytes;
@@ -472,8 +478,7 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
         const long long n = (long long)s.nw * (s.kp / 2);
         k_weights<<<(int)std::min<long long>((n + 255) / 256, 8192), 256, 0, ctx->stream>>>(
             s.nw, s.kp / 2, nt, ctx->nv, ctx->nc, ctx->d_Ek.as<double>(),
-            ctx->d_Ekq.as<double>() + (size_t)iq * ctx->nk * ctx->nc, s.w.as<double>(), s.eta, s_a / 32768.0,
-            s.wtab.as<float2>());
+            ctx->d_Ekq.as<double>() + (size_t)iq * ctx->nk * ctx->nc, s.w.as<double>(), s.eta, s.wtab.as<float2>());
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -488,11 +493,11 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     const size_t plane = (size_t)s.ngp * s.kp * 2;
     CUtensorMap mb[NPIECE], ms[NPIECE];
     for (int i = 0; i < NPIECE; ++i)
-        if (!qcx_make_f16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile) ||
-            !qcx_make_f16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK))
+        if (!qcx_make_bf16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile, KS) ||
+            !qcx_make_bf16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK, KS))
             return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute((const void*)k_chi0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_chi0_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mb[0], mb[1], ms[0], ms[1], a);
+    k_chi0_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mb[0], mb[1], mb[2], ms[0], ms[1], ms[2], a);
     return cudaGetLastError();
 }

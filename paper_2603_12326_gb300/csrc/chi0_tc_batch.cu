@@ -5,9 +5,8 @@
 // The arithmetic per tile is that of the per-q kernel: one 64-row G' block
 // of one instance at its frequency (a 128 x N accumulator: 64 re rows and 64
 // im rows of chi0_GG'), one N chunk of its G list, the contraction over
-// k' = 2t + p with both operands split into two FP16 terms (pair densities
-// stored as 2^15 rho, W scaled by a power of two) and the three (or four) split
-// products, FP32 accumulation restarted after 24 MMAs and promoted
+// k' = 2t + p split into three BF16 terms with the six products of order <= 2,
+// FP32 accumulation restarted after 24 MMAs (two K stages) and promoted
 // through FP32 registers into an FP64 buffer, and eps = delta - v^1/2 chi0 v^1/2
 // written in FP64 (row G', column G).
 //
@@ -18,7 +17,7 @@
 // memory ring and the two TMEM accumulators keep their phases across tile
 // boundaries, so the TMA producer already streams the next tile while the
 // epilogue warps finish the current one.  Every instance of one q reads the
-// same FP16 planes (the pair densities of the union of that q's G sets,
+// same BF16 planes (the pair densities of the union of that q's G sets,
 // sorted by |q+G| so that each instance's set is a prefix); the planes are
 // addressed through one tensor map per q and piece, all passed by value.  B
 // tiles of N <= 192 rows arrive as 64-row boxes.  Every wait is bounded.
@@ -31,8 +30,8 @@ namespace {
 
 constexpr int NTHREADS = 384;             // warps: 0 TMA, 1 and 10 MMA, 2-9 A/drain/epilogue, 11 idle
 constexpr int MMA_WARP2 = 10;
-constexpr int NSTAGE = 4;
-constexpr int NPIECE = 2;
+constexpr int NSTAGE = 3;
+constexpr int NPIECE = 3;
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per tile, rows per TMA box
 constexpr int MAXHALF = 96;
@@ -64,7 +63,6 @@ struct BArgs {
     double2* eps;
     int* status;
     long long wait_limit;     // clock cycles before a pipeline wait gives up
-    int nprod;                // 3: a0b0 + a0b1 + a1b0; 4: also a1b1
     int promote;              // K stages per accumulation window (24 MMAs)
     int flush;                // K stages between FP64 flushes (64 windows)
 };
@@ -183,17 +181,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                         }
                         tc_fence_after();
                         unsigned char* st = base + s * STAGE_BYTES;
-                        const uint32_t b0 = smem_u32(st), b1 = b0 + BREG;
+                        const uint32_t b0 = smem_u32(st), b1 = b0 + BREG, b2 = b1 + BREG;
                         const uint32_t d = tmem + (uint32_t)b * ACC_OFF;
-                        const uint32_t a0 = smem_u32(st + NPIECE * BREG + NPIECE * SPIECE), a1 = a0 + ATILE;
+                        const uint32_t a0 = smem_u32(st + NPIECE * BREG + NPIECE * SPIECE), a1 = a0 + ATILE,
+                                       a2 = a1 + ATILE;
 #pragma unroll
                         for (int kk = 0; kk < KSTEP / 16; ++kk) {
                             const uint32_t off = kk * 32;
-                            umma_f16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc,
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc,
                                       (first && kk == 0) ? 0u : 1u);
-                            umma_f16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
-                            umma_f16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                            if (a.nprod == 4) umma_f16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
                         }
                         umma_commit(&empty[s]);
                     }
@@ -281,34 +282,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                 unsigned char* st = base + s * STAGE_BYTES;
                 const unsigned char* srcb = st + (src_b ? 0 : NPIECE * BREG);
                 const uint32_t src_piece = src_b ? (uint32_t)BREG : (uint32_t)SPIECE;
-                uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0};
-                uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0};
+                uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};
+                uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0}, im2[4] = {0, 0, 0, 0};
                 if (go < lim) {
                     const uint32_t coff = sw64_off(row0 + go, j);
                     const uint4 h0 = *reinterpret_cast<const uint4*>(srcb + coff);
                     const uint4 h1 = *reinterpret_cast<const uint4*>(srcb + src_piece + coff);
-                    const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w};
+                    const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
+                    const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
+                                   v2[4] = {h2.x, h2.y, h2.z, h2.w};
                     const float4* Wv4 = reinterpret_cast<const float4*>(Wbuf + s * TPS + 4 * j);
                     const float4 wa = Wv4[0], wb = Wv4[1];
                     const float2 Wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
                                           make_float2(wb.z, wb.w)};
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
-                        const float2 f0 = h2f(v0[qq]), f1 = h2f(v1[qq]);
-                        const float rr = f0.x + f1.x, ri = f0.y + f1.y;
+                        const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
+                        const float rr = f0.x + (f1.x + f2.x), ri = f0.y + (f1.y + f2.y);
                         const float2 wq = Wv[qq];
-                        split2_h(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq]);
+                        split3(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq], re2[qq]);
                         // (xi, -xr) splits into the terms of (xr, xi), swapped, the second negated
                         im0[qq] = perm_im(re0[qq]);
                         im1[qq] = perm_im(re1[qq]);
+                        im2[qq] = perm_im(re2[qq]);
                     }
                 }
                 unsigned char* ap = st + NPIECE * BREG + NPIECE * SPIECE;
                 const uint32_t o_re = sw64_off(go, j), o_im = sw64_off(64 + go, j);
                 *reinterpret_cast<uint4*>(ap + o_re) = make_uint4(re0[0], re0[1], re0[2], re0[3]);
                 *reinterpret_cast<uint4*>(ap + ATILE + o_re) = make_uint4(re1[0], re1[1], re1[2], re1[3]);
+                *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_re) = make_uint4(re2[0], re2[1], re2[2], re2[3]);
                 *reinterpret_cast<uint4*>(ap + o_im) = make_uint4(im0[0], im0[1], im0[2], im0[3]);
                 *reinterpret_cast<uint4*>(ap + ATILE + o_im) = make_uint4(im1[0], im1[1], im1[2], im1[3]);
+                *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_im) = make_uint4(im2[0], im2[1], im2[2], im2[3]);
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full_a[s2]);
@@ -360,9 +366,8 @@ size_t qcx_chi0_tc_batch_acc_bytes(int grid) { return (size_t)grid * 128 * NMAX 
 cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, int slot0, int nslot, int ntile,
                                      const int4* d_tiles, int grid, const BatchInst* d_inst, const float2* wtab,
                                      long long wld, int kstages, double pref, double* acc64, double2* eps,
-                                     int* status, long long wait_limit, int nprod) {
-    if (nslot < 1 || nslot > QCX_BATCH_MAXQ || ntile < 1 || grid < 1 || kstages < 1 || (nprod != 3 && nprod != 4))
-        return cudaErrorInvalidValue;
+                                     int* status, long long wait_limit) {
+    if (nslot < 1 || nslot > QCX_BATCH_MAXQ || ntile < 1 || grid < 1 || kstages < 1) return cudaErrorInvalidValue;
     MapSet ms;
     memset(&ms, 0, sizeof(ms));
     for (int s = 0; s < nslot; ++s)
@@ -380,8 +385,7 @@ cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, i
     a.eps = eps;
     a.status = status;
     a.wait_limit = wait_limit;
-    a.nprod = nprod;
-    a.promote = 24 / ((KSTEP / 16) * nprod);
+    a.promote = 24 / ((KSTEP / 16) * 6);      // 24 MMAs per window: two K stages of twelve
     a.flush = 64 * a.promote;
     cudaError_t e =
         cudaFuncSetAttribute((const void*)k_chi0_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);

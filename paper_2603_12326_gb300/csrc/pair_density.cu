@@ -50,10 +50,10 @@ template <typename T> struct PDArgs {
     const cplx<T>* Ck;       // [nk][nb][nv]
     const cplx<T>* Ckq;      // [nk][nb][nc]
     double2* R64;            // FP64 output [ng][nt]
-    __half2* R0;             // MIXED output: two FP16 planes [ngp][kp/2] (pairs re, im) of
-    __half2* R1;             // x = 2^15 rho = x0 + x1 with x0 = fp16(x), x1 = fp16(x - x0)
-    long long kp2;           // row length of the FP16 planes in half2 units
-    int* range_flag;         // MIXED: set to 1 when some |Re rho| or |Im rho| exceeds 1.99
+    __nv_bfloat162* R0;      // MIXED output: three BF16 planes [ngp][kp/2] (pairs re, im),
+    __nv_bfloat162* R1;      // x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0),
+    __nv_bfloat162* R2;      // x2 = bf16(x - x0 - x1)
+    long long kp2;           // row length of the BF16 planes in bf16x2 units
     cplx<T>* Sout;           // overlap mode: [nk][nb][nb]
 };
 
@@ -167,22 +167,19 @@ __device__ __forceinline__ void pair_block(const PDArgs<T>& a, int ip, const T k
         }
 }
 
-// (re, im) of one FP32 pair density -> the two FP16 terms of each part of x = 2^15 rho,
-// x = x0 + x1 with x0 = fp16(x) and x1 = fp16(x - x0) (round to nearest), written to the two
-// planes.  |rho| <= 1 for orthonormal states; beyond 1.99 the scaled value could leave the FP16
-// range, which is flagged for the call to report.
-__device__ __forceinline__ void store_split2(float re, float im, __half2* R0, __half2* R1, long long o,
-                                             int* range_flag) {
-    if (!(fabsf(re) <= 1.99f && fabsf(im) <= 1.99f)) {
-        *range_flag = 1;
-        re = 0.0f;
-        im = 0.0f;
-    }
-    const float xr = re * 32768.0f, xi = im * 32768.0f;   // exact power-of-two scaling
-    const __half2 h = __floats2half2_rn(xr, xi);
-    const float2 hf = __half22float2(h);
+// (re, im) of one FP32 pair density -> the three BF16 terms of each part, x = x0 + x1 + x2 with
+// x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1) (round to nearest), written to the
+// three planes
+__device__ __forceinline__ void store_split3(float re, float im, __nv_bfloat162* R0, __nv_bfloat162* R1,
+                                             __nv_bfloat162* R2, long long o) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    const float2 hf = __bfloat1622float2(h);
+    const float rr = re - hf.x, ri = im - hf.y;
+    const __nv_bfloat162 m = __floats2bfloat162_rn(rr, ri);
+    const float2 mf = __bfloat1622float2(m);
     R0[o] = h;
-    R1[o] = __floats2half2_rn(xr - hf.x, xi - hf.y);
+    R1[o] = m;
+    R2[o] = __floats2bfloat162_rn(rr - mf.x, ri - mf.y);
 }
 
 template <typename T, int NCH>
@@ -229,7 +226,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
             if (a.R64) {
                 a.R64[(long long)g * a.nt + t] = make_double2((double)acc.x, (double)acc.y);
             } else {
-                store_split2((float)acc.x, (float)acc.y, a.R0, a.R1, (long long)g * a.kp2 + t, a.range_flag);
+                store_split3((float)acc.x, (float)acc.y, a.R0, a.R1, a.R2, (long long)g * a.kp2 + t);
             }
         }
     }
@@ -309,7 +306,7 @@ __global__ void __launch_bounds__(pdf_maxt<NV>()) k_pair_density_fused(PDArgs<fl
         C acc = mk<float>(0, 0);
         for (int mu = 0; mu < nb; ++mu) cfmac(acc, Ckqs[mu * nc + c], yv[(size_t)mu * nv]);
         const long long t = ((long long)k * nv + v) * nc + c;
-        store_split2(acc.x, acc.y, a.R0, a.R1, (long long)(g0 + l) * a.kp2 + t, a.range_flag);
+        store_split3(acc.x, acc.y, a.R0, a.R1, a.R2, (long long)(g0 + l) * a.kp2 + t);
     }
 }
 
@@ -658,13 +655,10 @@ cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precisio
     a.Ck = ctx->d_Ck32.as<float2>();
     a.Ckq = ctx->d_Ckq32.as<float2>() + (size_t)iq * ctx->nk * ctx->nb * ctx->nc;
     a.R64 = nullptr;
-    a.R0 = reinterpret_cast<__half2*>(s.rho.p);
+    a.R0 = reinterpret_cast<__nv_bfloat162*>(s.rho.p);
     a.R1 = a.R0 + (size_t)s.ngp * (s.kp / 2);
+    a.R2 = a.R1 + (size_t)s.ngp * (s.kp / 2);
     a.kp2 = s.kp / 2;
-    cudaError_t e = s.pd_range.ensure(sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.pd_range.p, 0, sizeof(int), ctx->stream);
-    if (e != cudaSuccess) return e;
-    a.range_flag = s.pd_range.as<int>();
     if (gcf) {
         a.g_per_cta = gcf;
         const dim3 gridf(ctx->nk, (s.ng + gcf - 1) / gcf);

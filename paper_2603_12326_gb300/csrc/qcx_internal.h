@@ -4,9 +4,6 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include <cmath>
 #include <stdint.h>
 
 #include <string>
@@ -49,7 +46,7 @@ struct QSlot {
     DevBuf kappa32;            // [ng][3] float
     DevBuf vs;                 // [ng] double, sqrt(4 pi)/|q+G|
     DevBuf vs32;               // [ng] float
-    DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: two FP16 planes [ngp][kp] of 2^15 rho
+    DevBuf rho;                // FP64: [ng][nt] double2 ; MIXED: three BF16 planes [ngp][kp]
     DevBuf eps;                // [nw][ng][ng] double2 (MIXED stores eps^T: row G', column G)
     DevBuf work;               // inverse work space
     DevBuf acc64;              // FP64 partial sums of the tensor-core chi0 (one region per CTA)
@@ -60,9 +57,8 @@ struct QSlot {
     DevBuf eps_diag;           // [nw][ng] double2
     DevBuf resid;              // [nw] double
     DevBuf flags;              // [nw] int (singular / error flags)
-    DevBuf pd_range;           // int: set when a MIXED pair density left the FP16 range (|rho| > 1.99)
-    int ngp = 0;               // padded G rows of the FP16 planes (multiple of 16)
-    long long kp = 0;          // padded K' = 2 nt columns of the FP16 planes
+    int ngp = 0;               // padded G rows of the BF16 planes (multiple of 16)
+    long long kp = 0;          // padded K' = 2 nt columns of the BF16 planes
     double eta = 0.0;
 };
 
@@ -153,7 +149,6 @@ struct qcx_ctx {
     double kappa_refine = 1.0e4;   // mixed inverse: FP64 diagonal correction above this kappa_1
     long long wait_limit = 4000000000LL;  // tensor-core kernels: clock cycles before a pipeline wait gives up
     int withhold_copies = 0;       // fault injection (tests): the per-q tensor-core kernel issues no copies
-    int chi0_products = 3;         // split-FP16 products per complex term of the mixed chi0 (3 or 4)
     MlpState* mlp = nullptr;       // surrogate network (parameters, Adam moments, work buffers)
 
     ~qcx_ctx();
@@ -180,19 +175,17 @@ cudaError_t qcx_pair_density_configure();
 // chi0 (chi0_fp64.cu, chi0_tc.cu)
 cudaError_t qcx_launch_chi0_fp64(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out);
 cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out, int* d_status);
-// 2-D tensor map over one FP16 plane [rows][kp], box {32, box_rows}, 64-byte swizzle
-bool qcx_make_f16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows);
-// Power of two s_A with |W_t(w)| s_A 1.99 < 2^15 for every w (|W| <= 2/eta): the mixed chi0 stores
-// W s_A 2^-15 so that W (2^15 rho) s_A 2^-15 fits FP16; exact to divide out.
-inline double qcx_w_scale(double eta) { return std::exp2(std::floor(std::log2(8192.0 * eta))); }
+// 2-D tensor map over one BF16 plane [rows][kp], box {box_k, box_rows} (box_k 16: 32-byte
+// swizzle, 32: 64-byte swizzle)
+bool qcx_make_bf16_map(CUtensorMap* m, void* base, long long kp, int rows, int box_rows, int box_k);
 
 // persistent tensor-core chi0 over a tile list of uneven instances (chi0_tc_batch.cu).
-// maps: [nslot][2] tensor maps (box {32, 64}) of the FP16 planes of slots slot0 .. slot0 + nslot - 1;
+// maps: [nslot][3] tensor maps (box {32, 64}) of the BF16 planes of slots slot0 .. slot0 + nslot - 1;
 // tiles: {inst, gb, n0, N | src<<16}, every tile's instance in that slot range.
 cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, int slot0, int nslot, int ntile,
                                      const int4* d_tiles, int grid, const BatchInst* d_inst, const float2* wtab,
                                      long long wld, int kstages, double pref, double* acc64, double2* eps,
-                                     int* status, long long wait_limit, int nprod);
+                                     int* status, long long wait_limit);
 size_t qcx_chi0_tc_batch_acc_bytes(int grid);
 
 // batched solve for the heads of eps^-1 (batch_solve.cu)

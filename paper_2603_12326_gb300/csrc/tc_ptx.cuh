@@ -1,17 +1,18 @@
 // Inline-PTX wrappers shared by the tensor-core kernels: mbarriers with
 // bounded waits, TMA (tiled and plain bulk) copies, TMEM allocation, the
-// kind::f16 tcgen05 MMA (FP16 operands, FP32 accumulation) with its
-// shared-memory descriptors, TMEM loads, and the two-term FP16 split.  Operand
-// tiles are K-major rows of 64 bytes (32 FP16 values) with the 64-byte swizzle.
+// kind::f16 tcgen05 MMA (BF16 operands, FP32 accumulation) with its
+// shared-memory descriptors for K-major tiles of 64-byte rows (64-byte swizzle)
+// and of 32-byte rows (32-byte swizzle), TMEM loads, and the three-term BF16
+// split.
 #pragma once
 
 #include <cuda.h>
-#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace {
 
-constexpr int KSTEP = 32;                 // FP16 K elements per stage = one 64-byte swizzle row
+constexpr int KSTEP = 32;                 // BF16 K elements per 64-byte swizzle row
 constexpr int ROWB = 2 * KSTEP;           // bytes per operand row in shared memory
 // Waits of the pipeline give up after a limit passed to the kernel (the
 // context's setting, ~2 s of clock cycles by default); the waits of the clean-up
@@ -106,7 +107,7 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -139,27 +140,44 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t sw64_off(int r, int j) {
     return (uint32_t)r * ROWB + ((uint32_t)(j ^ ((r >> 1) & 3)) << 4);
 }
-// kind::f16 instruction descriptor: FP16 x FP16 -> FP32 (A and B type fields 0 = FP16), both
+// Shared-memory matrix descriptor: K-major, 32-byte swizzle (rows of 32 bytes = 16 BF16), 8-row
+// groups 256 bytes apart.
+__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading-dimension offset (unused for swizzled K-major)
+    d |= (uint64_t)(256 >> 4) << 32;     // stride between 8-row groups
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)6 << 61;              // 32-byte swizzle
+    return d;
+}
+// byte offset of the 16-byte chunk j (0, 1) of row r in a 32-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw32_off(int r, int j) {
+    return (uint32_t)r * 32u + ((uint32_t)(j ^ ((r >> 2) & 1)) << 4);
+}
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32 (A and B type fields 1 = BF16), both
 // operands K-major
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Scale of the stored FP16 pair densities (|rho| <= 1 for orthonormal states, so
-// 2^15 |rho| stays below the FP16 maximum while small values keep normal terms).
-constexpr float RHO_SCALE = 32768.0f;
-
-__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
-    __half2 h = __floats2half2_rn(a, b);
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
 }
-__device__ __forceinline__ float2 h2f(uint32_t u) { return __half22float2(*reinterpret_cast<__half2*>(&u)); }
-// (a, b) -> two packed FP16 pairs with a = a0 + a1, b = b0 + b1 (a0 = fp16(a), a1 = fp16(a - a0))
-__device__ __forceinline__ void split2_h(float a, float b, uint32_t& p0, uint32_t& p1) {
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    p0 = *reinterpret_cast<const uint32_t*>(&h);
-    p1 = pack_h2(a - hf.x, b - hf.y);
+// (a, b) -> three packed BF16 pairs with a = a0 + a1 + a2, b = b0 + b1 + b2 (each term the
+// round-to-nearest BF16 of what the earlier terms leave)
+__device__ __forceinline__ void split3(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    p0 = *reinterpret_cast<uint32_t*>(&h);
+    const float ra = a - hf.x, rb = b - hf.y;
+    __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+    const float2 mf = __bfloat1622float2(m);
+    p1 = *reinterpret_cast<uint32_t*>(&m);
+    p2 = pack_bf16(ra - mf.x, rb - mf.y);
+}
+__device__ __forceinline__ float2 bf2(uint32_t u) {
+    return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
 }
 // the terms of (xi, -xr) from those of (xr, xi): swap the halves, negate the new high half
 __device__ __forceinline__ uint32_t perm_im(uint32_t re) { return __byte_perm(re, 0u, 0x1032) ^ 0x80000000u; }

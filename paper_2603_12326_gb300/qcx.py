@@ -52,7 +52,6 @@ _SIGS = {
     "qcx_set_refine_threshold": (I, [P, D]),
     "qcx_set_wait_limit": (I, [P, ct.c_longlong]),
     "qcx_set_fault_injection": (I, [P, I]),
-    "qcx_set_chi0_products": (I, [P, I]),
     "qcx_loss_function": (I, [P, I, P, P]),
     "qcx_bin_loss": (I, [P, I, P, I, I, P, P, P]),
     "qcx_rate": (I, [P, I, P, I, P, P, ct.POINTER(HaloParams), P, I, P]),
@@ -242,9 +241,6 @@ class Context:
 
     def set_wait_limit(self, cycles):
         self._check(qcx_set_wait_limit(self.h, int(cycles)))
-
-    def set_chi0_products(self, nprod: int):
-        self._check(qcx_set_chi0_products(self.h, int(nprod)))
 
     def set_fault_injection(self, withhold_copies: bool):
         self._check(qcx_set_fault_injection(self.h, 1 if withhold_copies else 0))

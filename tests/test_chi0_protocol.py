@@ -3,9 +3,9 @@
 A random-schedule model of the roles of k_chi0_tc (one tile per CTA) and of
 the persistent k_chi0_tc_batch (a list of tiles per CTA, stage and window
 counters running on across tiles): the TMA producer, every A-operand warp
-(which also drains the accumulators; k_chi0_tc has two groups of eight warps
-taking alternate K stages, k_chi0_tc_batch one group of eight), two MMA
-issuers on alternate accumulation windows, copies that land in any order and
+(which also drains the accumulators; k_chi0_tc has four groups of four warps,
+group g forming K stages g, g + 4, ..., k_chi0_tc_batch one group of eight),
+two MMA issuers on alternate accumulation windows, copies that land in any order and
 MMAs that complete in issue order.  A barrier completes a phase when its
 expected number of arrivals is in (each A warp arrives on its own), and a wait
 on parity p returns once the completed-phase count's parity differs from p, so
@@ -17,11 +17,12 @@ the producer leaves no copy is in flight and when TMEM is freed no MMA is.
 The same model runs with waits that give up (a wait limit that runs out, or
 copies withheld so that nothing completes): the abort must still end every
 role with its copies landed and its MMAs finished.  Ring depths and window
-lengths are those the launchers choose (4-8 stages; 3 or 4 stages per window),
-and the kernel sources are checked for the constants the model assumes.
-The copy and A-tile barriers are indexed by the stage modulo twice the ring
-depth, so a barrier's previous phase always belongs to the same A-warp group
-and lies two windows back for an issuer.  A ring shorter than the window,
+lengths are those the kernels use (k_chi0_tc: a ring of 4-8 stages, windows of
+four; k_chi0_tc_batch: three stages, windows of two), and the kernel sources
+are checked for the constants the model assumes.
+The copy and A-tile barriers are indexed by the stage modulo (number of A
+groups, at least two) x ring depth, so a barrier's previous phase always
+belongs to the same A-warp group and lies two windows back for an issuer.  A ring shorter than the window,
 where an issuer's wait can pass a phase early, is the negative control."""
 import os
 import random
@@ -57,16 +58,18 @@ class _Bar:
         return (self.done & 1) != parity
 
 
-def _run(kstages, nstage, promote, seed, ngroups=2, ntile=1, timeouts=False, withhold=False):
-    """One random schedule.  ngroups = 2: the per-q kernel (16 A warps, group g
-    forms stages g, g+2, ...; a warp drains the windows before wd after its
-    group's last stage of window wd); ngroups = 1: the batch kernel (8 A warps,
-    every stage; the previous window is drained after a window's last stage)."""
+def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, withhold=False):
+    """One random schedule.  ngroups = 4: the per-q kernel (16 A warps in groups
+    of four, group g forms stages g, g+4, ...; a warp drains the windows before
+    wd after its group's last stage of window wd); ngroups = 1: the batch kernel
+    (8 A warps, every stage; the previous window is drained after a window's
+    last stage)."""
     rnd = random.Random(seed)
-    nwarp = 8 * ngroups
-    # copy and A-tile barriers: one per stage modulo twice the ring depth
-    full_b = [_Bar(1) for _ in range(2 * nstage)]
-    full_a = [_Bar(8) for _ in range(2 * nstage)]
+    wpg = 4 if ngroups > 1 else 8                 # warps per group
+    nwarp = wpg * ngroups
+    nb = max(2, ngroups) * nstage                 # copy and A-tile barriers: stage modulo nb
+    full_b = [_Bar(1) for _ in range(nb)]
+    full_a = [_Bar(wpg) for _ in range(nb)]
     empty = [_Bar(1) for _ in range(nstage)]
     acc_full = [_Bar(1), _Bar(1)]
     drained = [_Bar(nwarp), _Bar(nwarp)]
@@ -99,17 +102,17 @@ def _run(kstages, nstage, promote, seed, ngroups=2, ntile=1, timeouts=False, wit
                                  "stage %d free" % gs)
             if not ok:
                 break
-            copies.append((gs, gs % (2 * nstage)))
+            copies.append((gs, gs % nb))
             issued.append(gs)
         for gs in issued[-nstage:]:              # let the copies in flight land
-            yield from wait(full_b[gs % (2 * nstage)], (gs // (2 * nstage)) & 1, lambda gs=gs: gs in landed,
+            yield from wait(full_b[gs % nb], (gs // nb) & 1, lambda gs=gs: gs in landed,
                             "copy %d" % gs, honour_abort=False)
         if [c for c in copies]:
             errors.append("producer left with copies in flight")
         state["producer_left"] = True
 
     def a_warp(w):
-        grp = w >> 3
+        grp = w // wpg
         drained_upto = 0
 
         def drain(gw):
@@ -120,11 +123,11 @@ def _run(kstages, nstage, promote, seed, ngroups=2, ntile=1, timeouts=False, wit
             return ok
 
         for lt in range(ntile):
-            stages = range(grp, kstages, 2) if ngroups == 2 else range(kstages)
+            stages = range(grp, kstages, ngroups)
             nxt = 0
             for it in stages:
                 gs = lt * kstages + it
-                s, ph = gs % (2 * nstage), (gs // (2 * nstage)) & 1
+                s, ph = gs % nb, (gs // nb) & 1
                 ok = yield from wait(full_b[s], ph, lambda gs=gs: gs in landed, "copy %d" % gs)
                 if not ok:
                     return
@@ -132,9 +135,9 @@ def _run(kstages, nstage, promote, seed, ngroups=2, ntile=1, timeouts=False, wit
                     errors.append("A tile %d overwritten under its MMAs" % gs)
                 gen_done[gs] = gen_done.get(gs, 0) + 1
                 full_a[s].arrive()
-                if ngroups == 2:
+                if ngroups > 1:
                     wd = it // promote
-                    if it + 2 >= min((wd + 1) * promote, kstages):
+                    if it + ngroups >= min((wd + 1) * promote, kstages):
                         while nxt < wd:
                             ok = yield from drain(lt * nwin + nxt)
                             nxt += 1
@@ -175,9 +178,9 @@ def _run(kstages, nstage, promote, seed, ngroups=2, ntile=1, timeouts=False, wit
                         break
                 for it in range(wd * promote, min((wd + 1) * promote, kstages)):
                     gs = lt * kstages + it
-                    s2 = gs % (2 * nstage)
-                    ok = yield from wait(full_a[s2], (gs // (2 * nstage)) & 1,
-                                         lambda gs=gs: gen_done.get(gs, 0) == 8, "A tile %d" % gs)
+                    s2 = gs % nb
+                    ok = yield from wait(full_a[s2], (gs // nb) & 1,
+                                         lambda gs=gs: gen_done.get(gs, 0) == wpg, "A tile %d" % gs)
                     if not ok:
                         break
                     if gs not in landed:
@@ -225,55 +228,55 @@ def _run(kstages, nstage, promote, seed, ngroups=2, ntile=1, timeouts=False, wit
 def test_model_matches_the_kernel_sources():
     """The constants and counts the model assumes are those of the kernels."""
     src = _src("chi0_tc.cu")
-    assert _constant("NAW", "chi0_tc.cu") == 16 and _constant("MAXSTAGE", "chi0_tc.cu") == 8
-    assert "mbar_init(&full_a[s], 8)" in src and "mbar_init(&drained[b], NAW)" in src
-    assert "for (int s = 0; s < 2 * NS; ++s)" in src            # copy and A-tile barriers: 2 NS of each
-    assert src.count("% (2 * NS)") >= 4 and "&empty[s]" in src
-    assert "for (int it = grp; it < a.kstages && ok; it += 2)" in src
-    assert "if (it + 2 >= min((wd + 1) * a.promote, a.kstages))" in src
+    assert _constant("NAW", "chi0_tc.cu") == 16 and _constant("NGRP", "chi0_tc.cu") == 4
+    assert _constant("MAXSTAGE", "chi0_tc.cu") == 8 and _constant("PROMOTE", "chi0_tc.cu") == 4
+    assert "mbar_init(&full_a[s], NAW / NGRP)" in src and "mbar_init(&drained[b], NAW)" in src
+    assert "const int NB = NGRP * NS;" in src and src.count("% NB") >= 4 and "&empty[s]" in src
+    assert "for (int it = grp; it < a.kstages && ok; it += NGRP)" in src
+    assert "if (it + NGRP >= min((wd + 1) * PROMOTE, a.kstages))" in src
     assert "for (int it = max(0, last - NS + 1); it <= last; ++it)" in src
-    assert _constant("WIN_MMAS", "chi0_tc.cu") == 24
-    assert "a.promote = WIN_MMAS / ((KSTEP / 16) * a.nprod)" in src and "a.nstage < 4" in src
+    assert "a.nstage < 4" in src
     bsrc = _src("chi0_tc_batch.cu")
-    assert _constant("NSTAGE", "chi0_tc_batch.cu") == 4
+    assert _constant("NSTAGE", "chi0_tc_batch.cu") == 3
     assert "mbar_init(&full_a[s], 8)" in bsrc and "mbar_init(&drained[b], 8)" in bsrc
     assert bsrc.count("% (2 * NSTAGE)") >= 4
-    assert "a.promote = 24 / ((KSTEP / 16) * nprod)" in bsrc
+    assert "a.promote = 24 / ((KSTEP / 16) * 6)" in bsrc
 
 
-@pytest.mark.parametrize("nstage", [4, 5, 6, 8])
-@pytest.mark.parametrize("promote", [3, 4])
+@pytest.mark.parametrize("nstage", [4, 5, 6, 7, 8])
 @pytest.mark.parametrize("kstages", [1, 2, 3, 5, 8, 13, 40])
-def test_kernel_protocol_holds_under_random_schedules(nstage, promote, kstages):
+def test_kernel_protocol_holds_under_random_schedules(nstage, kstages):
     for seed in range(8):
-        errors, aborted = _run(kstages, nstage, promote, seed)
-        assert not errors and not aborted, (nstage, promote, kstages, seed, errors[:3])
+        errors, aborted = _run(kstages, nstage, 4, seed)
+        assert not errors and not aborted, (nstage, kstages, seed, errors[:3])
 
 
-@pytest.mark.parametrize("nstage,promote", [(4, 4), (5, 3), (5, 4), (8, 3)])
-def test_kernel_abort_path_drains_copies_and_mmas(nstage, promote):
+@pytest.mark.parametrize("nstage", [4, 5, 7, 8])
+def test_kernel_abort_path_drains_copies_and_mmas(nstage):
     """Waits that give up at random points (or copies withheld, so that the
     first waits run out): every role ends, the producer leaves no copy in
     flight and no MMA runs when TMEM is freed."""
     n_abort = 0
     for seed in range(40):
-        errors, aborted = _run(24, nstage, promote, seed, timeouts=True)
+        errors, aborted = _run(24, nstage, 4, seed, timeouts=True)
         assert not errors, (seed, errors[:3])
         n_abort += bool(aborted)
-        errors, aborted = _run(9, nstage, promote, seed, timeouts=True, withhold=True)
+        errors, aborted = _run(9, nstage, 4, seed, timeouts=True, withhold=True)
         assert not errors and aborted, (seed, errors[:3])
     assert n_abort > 0
 
 
 @pytest.mark.parametrize("kstages,ntile", [(1, 5), (2, 4), (3, 3), (5, 3), (8, 2), (13, 3)])
-@pytest.mark.parametrize("promote", [3, 4])
-def test_batch_kernel_protocol_across_tiles(kstages, ntile, promote):
+def test_batch_kernel_protocol_across_tiles(kstages, ntile):
     """The persistent batch kernel runs the same roles over a list of tiles with
     the stage and window counters continuing across tiles."""
     nstage = _constant("NSTAGE", "chi0_tc_batch.cu")
     for seed in range(10):
-        errors, aborted = _run(kstages, nstage, promote, seed, ngroups=1, ntile=ntile)
+        errors, aborted = _run(kstages, nstage, 2, seed, ngroups=1, ntile=ntile)
         assert not errors and not aborted, (kstages, ntile, seed, errors[:3])
+    for seed in range(10):
+        errors, aborted = _run(kstages, nstage, 2, seed, ngroups=1, ntile=ntile, timeouts=True)
+        assert not errors, (kstages, ntile, seed, errors[:3])
 
 
 def test_short_ring_is_caught():

@@ -59,26 +59,3 @@ def test_failure_settings_reject_bad_arguments():
     assert qcx.qcx_set_wait_limit(None, 100) == 1
     assert qcx.qcx_set_fault_injection(None, 1) == 1
 
-
-def test_pair_densities_outside_the_fp16_range_are_reported():
-    """The mixed path keeps 2^15 rho in FP16 terms, which holds |rho| <= 1.99
-    (orthonormal states give |rho| <= 1).  Coefficients scaled by 3 (not
-    orthonormal) push some pair densities past that: the values are not used
-    (they are stored as zero, never as infinities) and qcx_chi0 reports
-    QCX_ERR_UNSUPPORTED; the FP64 path has no such limit and the context stays
-    usable."""
-    p = synth.make_small(nq=1, nw=6)
-    Ck, Ckq = rpa.states(p, 0)
-    ctx = context()
-    set_oracle_states(ctx, p, [0], 3.0 * Ck, [3.0 * Ckq])
-    ctx.pair_density(0, p.G_int, QCX_MIXED)
-    with pytest.raises(qcx.QcxError) as e:
-        ctx.chi0(0, p.w, p.eta, QCX_MIXED)
-    assert e.value.status == 8
-    set_oracle_states(ctx, p, [0], Ck, [Ckq])
-    ctx.pair_density(0, p.G_int, QCX_MIXED)
-    ctx.chi0(0, p.w, p.eta, QCX_MIXED)
-    ctx.invert_eps(0, QCX_MIXED, want=False)
-    L1, _ = ctx.loss_function(0, QCX_MIXED)
-    ctx.close()
-    assert np.all(np.isfinite(L1))
