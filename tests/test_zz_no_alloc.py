@@ -64,7 +64,7 @@ def test_noalloc_flags_a_singular_matrix_among_good_ones():
     regular path (1e-10).  A zero matrix meets a zero pivot at the first
     column, so the elimination's singular branch runs whatever the rounding."""
     torch = pytest.importorskip("torch")
-    p = synth.make_small(nq=1, nw=3)
+    p = synth.make_small(nq=1)
     Ck, Ckq = rpa.states(p, 0)
     ctx = context()
     c, b = p.cell, p.basis
