@@ -12,35 +12,31 @@
 // operands are split into three BF16 terms x = x0 + x1 + x2 (x0 = bf16(x),
 // x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)); D accumulates in FP32 the six
 // products whose order is at most 2, a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0,
-// so each product carries ~2^-24 relative error.  (Two BF16 terms with three
-// or four products leave 2^-17 of every operand and miss 1e-4 on the loss with
-// local fields at some q; two FP16 terms, scaled by powers of two, missed it
-// too, although a host emulation that keeps FP16 subnormals meets it.)
-// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta)
-// is tabulated per q by k_weights with dE and w -+ dE in FP64 and fetched with
-// each K stage.
+// so each product carries ~2^-24 relative error (the two-term split's 2^-16
+// is too coarse once the inverse amplifies it by the condition number of eps).
+// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is tabulated per q by
+// k_weights with dE and w -+ dE in FP64 and fetched with each K stage.
 //
 // The tensor core's FP32 accumulation truncates, so long sums drift (about
 // 2^-24 of the running value per MMA, always toward zero).  The accumulator
-// is therefore restarted after 24 MMAs (four K stages of six products): TMEM
-// holds two buffers used in turn, the finished buffer is drained into FP32
-// registers (round to nearest), and every 64 windows the register partials are
-// added into an FP64 buffer owned by the CTA.  The Dyson step runs in FP64
-// from that buffer and eps is stored in FP64.
+// is therefore restarted every PROMOTE K stages: TMEM holds two buffers used
+// in turn, the finished buffer is drained into FP32 registers (round to
+// nearest), and every FLUSH stages the register partials are added into an
+// FP64 buffer owned by the CTA.  The Dyson step runs in FP64 from that
+// buffer and eps is stored in FP64.  (Two BF16 terms with three or four
+// products leave 2^-17 of every operand and miss 1e-4 on the loss with local
+// fields at some q; two FP16 terms, scaled by powers of two, missed it too,
+// although a host emulation that keeps FP16 subnormals meets it.)
 //
-// A K stage is 16 BF16 values (8 transitions): operand rows of 32 bytes with
-// the 32-byte swizzle, so a stage is small (B 18 KB, A 12 KB for N = 192) and
-// the ring holds 6-8 stages in flight.  CTA work item: one 64-row G' block,
-// one frequency (a 128 x N accumulator: 64 re rows and 64 im rows), one N chunk
-// of G.  Warp roles: warp 0 issues the TMA loads of a stage (B tile, the W
-// chunk and, when the G range is split, the A-source rows); warp 1 owns TMEM;
-// one thread of warp 1 issues the MMAs of the even accumulation windows and
-// one thread of warp 2 those of the odd windows; warps 3-18 form W rho and the
-// A tiles (four groups of four warps, group g taking the K stages g, g + 4,
-// ...), drain the accumulators (each warp a quarter of the columns of its lane
-// quadrant) and run the epilogue (eps = delta - v^1/2 chi0 v^1/2).  Every wait
-// is bounded: on timeout the kernel records an error status, lets its own
-// copies and MMAs finish, frees TMEM and returns.
+// CTA work item: one 64-row G' block, one frequency (a 128 x N accumulator:
+// 64 re rows and 64 im rows), one N chunk of G.  Warp roles: warp 0 issues
+// TMA loads of the B tiles (and, when the G range is split, of the A-source
+// rows); warp 1 owns TMEM; one thread of warp 1 issues the MMAs of the even
+// accumulation windows and one thread of warp 10 those of the odd windows;
+// warps 2-9 form W and the A tiles, drain the accumulators and run the
+// epilogue (eps = delta - v^1/2 chi0 v^1/2); warp 11 idles.  Every wait is bounded: on timeout the
+// kernel records an error status, lets its own copies and MMAs finish, frees
+// TMEM and returns.
 #include "qcx_internal.h"
 #include "tc_ptx.cuh"
 
@@ -48,32 +44,22 @@
 
 namespace {
 
+constexpr int NTHREADS = 384;                // warps: 0 TMA, 1 and 10 MMA, 2-9 A/drain/epilogue, 11 idle
+constexpr int MMA_WARP2 = 10;
+constexpr int NSTAGE = 3;
 constexpr int NPIECE = 3;                 // BF16 terms per operand
-constexpr int KS = 16;                    // BF16 K elements per stage (one 32-byte row)
-constexpr int RB = 2 * KS;                // bytes per operand row in shared memory
-constexpr int AW0 = 3;                    // first A/drain/epilogue warp
-constexpr int NAW = 16;                   // A/drain/epilogue warps
-constexpr int NGRP = 4;                   // A groups (four warps each) on alternate K stages
-constexpr int NTHREADS = (AW0 + NAW) * 32;
-constexpr int MMA_WARP2 = 2;
-constexpr int MAXSTAGE = 8;               // ring depth at most
-constexpr int NBAR = NGRP * MAXSTAGE;     // copy / A-tile barriers: stage mod NGRP * ring depth
-constexpr int ATILE = 128 * RB;           // one 128-row A piece
+constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per half tile
-constexpr int PROMOTE = 4;                // K stages per accumulation window (4 x 6 = 24 MMAs)
-constexpr int FLUSH = 64 * PROMOTE;       // K stages between FP64 flushes of the register partials
-constexpr int MAXN = 192;                 // largest N tile
-constexpr int MAXC = 48;                  // accumulator columns one thread drains (N/4 rounded up to 8)
+constexpr int PROMOTE = 2;                // K stages accumulated in one TMEM buffer
+constexpr int FLUSH = 128;                // stages between FP64 flushes of the register partials
+constexpr int MAXHALF = 96;               // columns of the accumulator one thread drains (n_tile/2)
 constexpr int SMEM_LIMIT = 232448;
-constexpr int TPS = KS / 2;               // transitions per stage
-constexpr int WBYTES = TPS * (int)sizeof(float2);
+constexpr int PREFETCH = 4;               // K stages between the L2 prefetch of a stage and its copy
 
 struct TcArgs {
     int ng, nw, nv, nc;
     long long nt;
     int n_tile, n_gb, kstages, src_from_b;
-    int nstage;           // ring depth
-    uint32_t stage_bytes; // one ring stage (1024-aligned)
     uint32_t acc_off, tmem_cols;      // second TMEM buffer column, columns allocated
     const float2* wtab;   // [nw][kp/2] W_t(w) in FP32 (tabulated with FP64 dE)
     long long wld;        // row length of wtab
@@ -87,9 +73,7 @@ struct TcArgs {
     int withhold;           // fault injection: issue no copies
 };
 
-// 19 warps, one CTA per SM: an SM sub-partition holds 16384 registers and five of the warps, so at most
-// 96 registers per thread
-__global__ void __maxnreg__(96)
+__global__ void __launch_bounds__(NTHREADS, 1)
     k_chi0_tc(const __grid_constant__ CUtensorMap mb0, const __grid_constant__ CUtensorMap mb1,
               const __grid_constant__ CUtensorMap mb2, const __grid_constant__ CUtensorMap ms0,
               const __grid_constant__ CUtensorMap ms1, const __grid_constant__ CUtensorMap ms2, TcArgs a) {
@@ -98,36 +82,38 @@ __global__ void __maxnreg__(96)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x / a.nw, iw = blockIdx.x % a.nw;
     const int n0 = blockIdx.y * a.n_tile;
-    const int NS = a.nstage;
-    const int NB = NGRP * NS;                                   // copy / A-tile barriers in use
-    const uint32_t bbytes = (uint32_t)a.n_tile * RB;            // one B piece
-    const uint32_t spiece = (uint32_t)GBLK * RB;                // one A-source piece
+    const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;          // one B piece
+    const uint32_t spiece = (uint32_t)GBLK * ROWB;              // one A-source piece
     const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * spiece;
     const uint32_t aoff = NPIECE * bbytes + sbytes;             // A pieces start here in a stage
-    const uint32_t woff = aoff + NPIECE * ATILE;                // the stage's W chunk
-    unsigned char* tail = base + (size_t)NS * a.stage_bytes;
-    // The copy and A-tile barriers of K stage it are number it mod NGRP NS (ring slot it mod NS): the
-    // previous phase of such a barrier then belongs to the same A-warp group, and lies at least two
-    // accumulation windows back for an MMA issuer, so no wait can pass a phase early.
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
-    uint64_t* full_b = bars;                   // [NB] copies of the stage landed
-    uint64_t* full_a = bars + NBAR;            // [NB] A tiles of the stage written (one group: 4 warps)
-    uint64_t* empty = bars + 2 * NBAR;         // [NS] MMAs of the slot done (slot reusable)
-    uint64_t* acc_full = empty + MAXSTAGE;     // [2] TMEM buffer holds a finished window
-    uint64_t* drained = acc_full + 2;          // [2] TMEM buffer read out (16 warps)
-    uint64_t* mma_done = drained + 2;          // every issued MMA finished
+    const uint32_t stage_bytes = aoff + NPIECE * ATILE;
+    constexpr int TPS = KSTEP / 2;                              // transitions per stage
+    unsigned char* tail = base + NSTAGE * stage_bytes;
+    float2* Wbuf = reinterpret_cast<float2*>(tail);             // [NSTAGE][TPS]
+    // The copy and A-tile barriers of K stage it are number it mod 2 NSTAGE (ring slot it mod
+    // NSTAGE): the previous phase of such a barrier lies at least two accumulation windows back
+    // for an MMA issuer, so no wait can pass a phase early.
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tail + NSTAGE * TPS * sizeof(float2));
+    uint64_t* full_b = bars;                     // [2 NSTAGE] TMA landed
+    uint64_t* full_a = bars + 2 * NSTAGE;        // [2 NSTAGE] A tiles written (8 warps)
+    uint64_t* empty = bars + 4 * NSTAGE;         // [NSTAGE] MMAs of the slot done (smem reusable)
+    uint64_t* acc_full = bars + 5 * NSTAGE;      // [2] TMEM buffer holds a finished window
+    uint64_t* drained = acc_full + 2;        // [2] TMEM buffer read out (8 warps)
+    uint64_t* mma_done = drained + 2;        // every issued MMA finished
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NB; ++s) {
+        for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(&full_b[s], 1);
-            mbar_init(&full_a[s], NAW / NGRP);
+            mbar_init(&full_a[s], 8);
+            mbar_init(&full_b[s + NSTAGE], 1);
+            mbar_init(&full_a[s + NSTAGE], 8);
+            mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < NS; ++s) mbar_init(&empty[s], 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&drained[b], NAW);
+            mbar_init(&drained[b], 8);
         }
         mbar_init(mma_done, 2);     // one commit per MMA issuer
         *abort_flag = 0;
@@ -138,52 +124,50 @@ __global__ void __maxnreg__(96)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
-            const int pf = NS + 2;          // K stages between the L2 prefetch of a stage and its copy
             // a stage's lines are requested into L2 a few stages before its copy is issued
             auto prefetch = [&](int it) {
-                bulk_prefetch(a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, WBYTES);
-                tma_prefetch_2d(&mb0, it * KS, n0);
-                tma_prefetch_2d(&mb1, it * KS, n0);
-                tma_prefetch_2d(&mb2, it * KS, n0);
+                bulk_prefetch(a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2));
+                tma_prefetch_2d(&mb0, it * KSTEP, n0);
+                tma_prefetch_2d(&mb1, it * KSTEP, n0);
+                tma_prefetch_2d(&mb2, it * KSTEP, n0);
                 if (!a.src_from_b) {
-                    tma_prefetch_2d(&ms0, it * KS, gb * GBLK);
-                    tma_prefetch_2d(&ms1, it * KS, gb * GBLK);
-                    tma_prefetch_2d(&ms2, it * KS, gb * GBLK);
+                    tma_prefetch_2d(&ms0, it * KSTEP, gb * GBLK);
+                    tma_prefetch_2d(&ms1, it * KSTEP, gb * GBLK);
+                    tma_prefetch_2d(&ms2, it * KSTEP, gb * GBLK);
                 }
             };
-            for (int it = 0; it < pf && it < a.kstages; ++it) prefetch(it);
+            for (int it = 0; it < PREFETCH && it < a.kstages; ++it) prefetch(it);
             int last = -1;
             // with copies withheld (fault injection for tests) nothing is issued, so the
             // consumers' first waits run out and the kernel reports a timeout
-            const int nissue = a.withhold ? 0 : a.kstages;
-            for (int it = 0; it < nissue; ++it) {
-                if (it + pf < a.kstages) prefetch(it + pf);
-                const int s = it % NS;
-                if (!mbar_wait(&empty[s], ((uint32_t)(it / NS) & 1u) ^ 1u, abort_flag, a.status, a.wait_limit)) break;
-                uint64_t* fb = &full_b[it % NB];
-                unsigned char* st = base + (size_t)s * a.stage_bytes;
-                mbar_arrive_tx(fb, NPIECE * bbytes + sbytes + WBYTES);
-                bulk_load(st + woff, a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, WBYTES, fb);
-                tma_load_2d(st, &mb0, fb, it * KS, n0);
-                tma_load_2d(st + bbytes, &mb1, fb, it * KS, n0);
-                tma_load_2d(st + 2 * bbytes, &mb2, fb, it * KS, n0);
+            for (int it = 0; it < (a.withhold ? 0 : a.kstages); ++it) {
+                const int s = it % NSTAGE;
+                const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+                if (it + PREFETCH < a.kstages) prefetch(it + PREFETCH);
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status, a.wait_limit)) break;
+                uint64_t* fb = &full_b[it % (2 * NSTAGE)];
+                unsigned char* st = base + s * stage_bytes;
+                mbar_arrive_tx(fb, NPIECE * bbytes + sbytes + TPS * (uint32_t)sizeof(float2));
+                bulk_load(Wbuf + s * TPS, a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2), fb);
+                tma_load_2d(st, &mb0, fb, it * KSTEP, n0);
+                tma_load_2d(st + bbytes, &mb1, fb, it * KSTEP, n0);
+                tma_load_2d(st + 2 * bbytes, &mb2, fb, it * KSTEP, n0);
                 if (!a.src_from_b) {
                     unsigned char* sp = st + NPIECE * bbytes;
-                    tma_load_2d(sp, &ms0, fb, it * KS, gb * GBLK);
-                    tma_load_2d(sp + spiece, &ms1, fb, it * KS, gb * GBLK);
-                    tma_load_2d(sp + 2 * spiece, &ms2, fb, it * KS, gb * GBLK);
+                    tma_load_2d(sp, &ms0, fb, it * KSTEP, gb * GBLK);
+                    tma_load_2d(sp + spiece, &ms1, fb, it * KSTEP, gb * GBLK);
+                    tma_load_2d(sp + 2 * spiece, &ms2, fb, it * KSTEP, gb * GBLK);
                 }
                 last = it;
             }
-            // let every copy still in flight (at most the last NS stages) land before the CTA can exit
-            for (int it = max(0, last - NS + 1); it <= last; ++it)
-                mbar_wait(&full_b[it % NB], (uint32_t)(it / NB) & 1u, abort_flag, a.status, CLEANUP_WAIT_LIMIT,
-                          false);
+            // let every copy still in flight (at most the last NSTAGE stages) land before the CTA can exit
+            for (int it = max(0, last - NSTAGE + 1); it <= last; ++it)
+                mbar_wait(&full_b[it % (2 * NSTAGE)], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag, a.status,
+                          CLEANUP_WAIT_LIMIT, false);
         }
     } else if (warp == 1 || warp == MMA_WARP2) {
         // ---------------------------------------------------------- MMA issuers
@@ -194,6 +178,7 @@ __global__ void __maxnreg__(96)
         if (lane == 0) {
             const int par = warp == 1 ? 0 : 1;
             const uint32_t idesc = make_idesc(128, a.n_tile);
+            const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
             bool ok = true;
             for (int win = par; win < nwin && ok; win += 2) {
                 const int b = win & 1;
@@ -202,23 +187,29 @@ __global__ void __maxnreg__(96)
                     break;
                 const int it1 = min((win + 1) * PROMOTE, a.kstages);
                 for (int it = win * PROMOTE; it < it1; ++it) {
-                    const int s = it % NS;
+                    const int s = it % NSTAGE;
+                    const bool first = it == win * PROMOTE;
                     // the A warps arrive only after they saw this stage's copies land
-                    if (!mbar_wait(&full_a[it % NB], (uint32_t)(it / NB) & 1u, abort_flag, a.status, a.wait_limit)) {
+                    if (!mbar_wait(&full_a[it % (2 * NSTAGE)], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag,
+                                   a.status, a.wait_limit)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    unsigned char* st = base + (size_t)s * a.stage_bytes;
+                    unsigned char* st = base + s * stage_bytes;
                     const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes, b2 = b1 + bbytes;
                     const uint32_t d = tmem + (uint32_t)b * a.acc_off;
                     const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE, a2 = a1 + ATILE;
-                    umma_bf16(d, sw32_desc(a0), sw32_desc(b0), idesc, it == win * PROMOTE ? 0u : 1u);
-                    umma_bf16(d, sw32_desc(a0), sw32_desc(b1), idesc, 1u);
-                    umma_bf16(d, sw32_desc(a1), sw32_desc(b0), idesc, 1u);
-                    umma_bf16(d, sw32_desc(a0), sw32_desc(b2), idesc, 1u);
-                    umma_bf16(d, sw32_desc(a1), sw32_desc(b1), idesc, 1u);
-                    umma_bf16(d, sw32_desc(a2), sw32_desc(b0), idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < KSTEP / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
+                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                        umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (ok) umma_commit(&acc_full[b]);
@@ -227,47 +218,45 @@ __global__ void __maxnreg__(96)
             umma_commit(mma_done);
             mbar_wait(mma_done, 0, abort_flag, a.status, CLEANUP_WAIT_LIMIT, false);
         }
-    } else {
+    } else if (warp < MMA_WARP2) {
         // --------------------------------- A generation, accumulator drain, epilogue
-        const int wa = warp - AW0;          // 0..15
-        const int grp = wa >> 2;            // this warp's group forms the A tiles of stages grp, grp + 4, ...
-        const int gi = ((wa & 3) << 5) | lane;   // 0..127 within the group
-        const int j = gi & 1;               // 16-byte chunk = 4 transitions
-        const int go = gi >> 1;             // G' offset in the block (0..63)
+        const int wi = warp - 2;            // 0..7
+        const int g = threadIdx.x - 64;     // 0..255
+        const int j = g & 3;                // 16-byte chunk = 4 transitions
+        const int go = g >> 2;              // G' offset in the block (0..63)
         const int Gp = gb * GBLK + go;
-        // drain mapping: TMEM lane quadrant q (fixed by the warp's rank modulo 4), column slice cs
-        const int q = warp & 3, cs = wa >> 2;
-        const int cw = ((a.n_tile + 31) / 32) * 8;          // columns per slice (multiple of 8)
-        const int c0 = min(cs * cw, a.n_tile), c1 = min(c0 + cw, a.n_tile);
-        const int ncol8 = (c1 - c0) >> 3;
+        // drain mapping: lane quadrant q, column half hc
+        const int q = warp & 3, hc = wi >> 2;
+        const int half = a.n_tile >> 1;
+        const int nch8 = half >> 3;         // 8-column TMEM loads per thread
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const int row = q * 32 + lane;      // accumulator row: 0..63 re, 64..127 im
-        double* acc64 = a.acc64 + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 + row) * a.n_tile + c0;
-        float part[MAXC];
+        double* acc64 = a.acc64 + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 + row) * a.n_tile + hc * half;
+        const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
+        float part[MAXHALF];
 #pragma unroll
-        for (int i = 0; i < MAXC; ++i) part[i] = 0.0f;
+        for (int i = 0; i < MAXHALF; ++i) part[i] = 0.0f;
         bool ok = true;
         int flushed = 0;                    // FP64 region initialised?
-        int next_drain = 0;                 // first window this warp has not drained
 
         auto drain = [&](int wd) -> bool {
             const int b = wd & 1;
             if (!warp_wait(&acc_full[b], (uint32_t)(wd >> 1) & 1u, abort_flag, a.status, a.wait_limit)) return false;
             tc_fence_after();
-            const uint32_t tb = tmem + lane_off + (uint32_t)b * a.acc_off + (uint32_t)c0;
+            const uint32_t tb = tmem + lane_off + (uint32_t)b * a.acc_off + (uint32_t)(hc * half);
             // 8-column loads in pairs, one wait per pair (compile-time register indices)
 #pragma unroll
-            for (int g2 = 0; g2 < MAXC / 16; ++g2) {
+            for (int grp = 0; grp < MAXHALF / 16; ++grp) {
                 uint32_t r[2][8];
 #pragma unroll
                 for (int u = 0; u < 2; ++u)
-                    if (g2 * 2 + u < ncol8) tmem_ld8(tb + (uint32_t)((g2 * 2 + u) * 8), r[u]);
+                    if (grp * 2 + u < nch8) tmem_ld8(tb + (uint32_t)((grp * 2 + u) * 8), r[u]);
                 tmem_wait_ld();
 #pragma unroll
                 for (int u = 0; u < 2; ++u)
-                    if (g2 * 2 + u < ncol8) {
+                    if (grp * 2 + u < nch8) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) part[(g2 * 2 + u) * 8 + i] += __uint_as_float(r[u][i]);
+                        for (int i = 0; i < 8; ++i) part[(grp * 2 + u) * 8 + i] += __uint_as_float(r[u][i]);
                     }
             }
             tc_fence_before();
@@ -275,8 +264,8 @@ __global__ void __maxnreg__(96)
             if (lane == 0) mbar_arrive(&drained[b]);
             if (((wd + 1) * PROMOTE) % FLUSH == 0 || wd + 1 == nwin) {
 #pragma unroll
-                for (int c = 0; c < MAXC; ++c) {
-                    if (c < c1 - c0) {
+                for (int c = 0; c < MAXHALF; ++c) {
+                    if (c < half) {
                         acc64[c] = (flushed ? acc64[c] : 0.0) + (double)part[c];
                         part[c] = 0.0f;
                     }
@@ -286,58 +275,62 @@ __global__ void __maxnreg__(96)
             return true;
         };
 
-        for (int it = grp; it < a.kstages && ok; it += NGRP) {
-            const int s = it % NS;
-            const int sb = it % NB;
+        for (int it = 0; it < a.kstages && ok; ++it) {
+            const int s = it % NSTAGE;
+            const int s2 = it % (2 * NSTAGE);
             // the producer issued this stage's copies only after the MMAs of its previous use
             // finished, so a landed stage is also free to overwrite
-            if (!(ok = warp_wait(&full_b[sb], (uint32_t)(it / NB) & 1u, abort_flag, a.status, a.wait_limit))) break;
-            unsigned char* st = base + (size_t)s * a.stage_bytes;
+            if (!(ok = warp_wait(&full_b[s2], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag, a.status,
+                                 a.wait_limit)))
+                break;
+            unsigned char* st = base + s * stage_bytes;
             const unsigned char* srcb = a.src_from_b ? st : st + NPIECE * bbytes;
             const uint32_t src_piece = a.src_from_b ? bbytes : spiece;
-            uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};   // re row terms
+            uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};   // re row
+            uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0}, im2[4] = {0, 0, 0, 0};   // im row
             if (Gp < a.ng) {
                 const int srow = a.src_from_b ? Gp : go;
-                const uint32_t coff = sw32_off(srow, j);
+                const uint32_t coff = sw64_off(srow, j);
                 const uint4 h0 = *reinterpret_cast<const uint4*>(srcb + coff);
                 const uint4 h1 = *reinterpret_cast<const uint4*>(srcb + src_piece + coff);
                 const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
                 const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
                                v2[4] = {h2.x, h2.y, h2.z, h2.w};
-                const float4* Wv4 = reinterpret_cast<const float4*>(st + woff) + 2 * j;
-                const float4 wa4 = Wv4[0], wb4 = Wv4[1];
-                const float2 Wv[4] = {make_float2(wa4.x, wa4.y), make_float2(wa4.z, wa4.w),
-                                      make_float2(wb4.x, wb4.y), make_float2(wb4.z, wb4.w)};
+                const float4* Wv4 = reinterpret_cast<const float4*>(Wbuf + s * TPS + 4 * j);
+                const float4 wa = Wv4[0], wb = Wv4[1];
+                const float2 Wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                                      make_float2(wb.z, wb.w)};
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
                     const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
                     const float rr = f0.x + (f1.x + f2.x), ri = f0.y + (f1.y + f2.y);
                     const float2 wq = Wv[qq];
-                    split3(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq], re2[qq]);
+                    const float xr = wq.x * rr - wq.y * ri;
+                    const float xi = wq.x * ri + wq.y * rr;
+                    split3(xr, xi, re0[qq], re1[qq], re2[qq]);
+                    // (xi, -xr) splits into the same terms as (xr, xi), swapped, the second negated
+                    im0[qq] = perm_im(re0[qq]);
+                    im1[qq] = perm_im(re1[qq]);
+                    im2[qq] = perm_im(re2[qq]);
                 }
             }
             unsigned char* ap = st + aoff;
-            const uint32_t o_re = sw32_off(go, j), o_im = sw32_off(64 + go, j);
+            const uint32_t o_re = sw64_off(go, j), o_im = sw64_off(64 + go, j);
             *reinterpret_cast<uint4*>(ap + o_re) = make_uint4(re0[0], re0[1], re0[2], re0[3]);
             *reinterpret_cast<uint4*>(ap + ATILE + o_re) = make_uint4(re1[0], re1[1], re1[2], re1[3]);
             *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_re) = make_uint4(re2[0], re2[1], re2[2], re2[3]);
-            // (xi, -xr) splits into the same terms as (xr, xi), swapped, the second negated
-            *reinterpret_cast<uint4*>(ap + o_im) =
-                make_uint4(perm_im(re0[0]), perm_im(re0[1]), perm_im(re0[2]), perm_im(re0[3]));
-            *reinterpret_cast<uint4*>(ap + ATILE + o_im) =
-                make_uint4(perm_im(re1[0]), perm_im(re1[1]), perm_im(re1[2]), perm_im(re1[3]));
-            *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_im) =
-                make_uint4(perm_im(re2[0]), perm_im(re2[1]), perm_im(re2[2]), perm_im(re2[3]));
+            *reinterpret_cast<uint4*>(ap + o_im) = make_uint4(im0[0], im0[1], im0[2], im0[3]);
+            *reinterpret_cast<uint4*>(ap + ATILE + o_im) = make_uint4(im1[0], im1[1], im1[2], im1[3]);
+            *reinterpret_cast<uint4*>(ap + 2 * ATILE + o_im) = make_uint4(im2[0], im2[1], im2[2], im2[3]);
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&full_a[sb]);
-            // after this group's last stage of window wd, drain the windows before wd (their MMAs
-            // finished long ago, so the drain does not wait on the tensor pipe)
-            const int wd = it / PROMOTE;
-            if (it + NGRP >= min((wd + 1) * PROMOTE, a.kstages))
-                while (ok && next_drain < wd) ok = drain(next_drain++);
+            if (lane == 0) mbar_arrive(&full_a[s2]);
+            // drain the previous window once this window's A tiles are all queued (its
+            // MMAs finished long ago, so the drain does not wait on the tensor pipe)
+            if (it % PROMOTE == PROMOTE - 1 && it >= PROMOTE && !(ok = drain(it / PROMOTE - 1))) break;
         }
-        while (ok && next_drain < nwin) ok = drain(next_drain++);
+        if (ok && nwin >= 2 && (a.kstages - 1) % PROMOTE != PROMOTE - 1) ok = drain(nwin - 2);
+        if (ok) ok = drain(nwin - 1);
         // -------------------------------------------------------------- epilogue
         if (ok) {
             const int cpart = row >> 6, gro = row & 63;
@@ -346,8 +339,8 @@ __global__ void __maxnreg__(96)
                 const double vsp = a.vs[Gr];
                 const size_t rowoff = ((size_t)iw * a.ng + Gr) * a.ng;
                 double* plane = reinterpret_cast<double*>(a.eps) + cpart;
-                for (int col = 0; col < c1 - c0; ++col) {
-                    const int G = n0 + c0 + col;
+                for (int col = 0; col < half; ++col) {
+                    const int G = n0 + hc * half + col;
                     if (G < a.ng) {
                         const double ch = a.pref * acc64[col];
                         plane[2 * (rowoff + G)] = (cpart == 0 && G == Gr ? 1.0 : 0.0) - vsp * a.vs[G] * ch;
@@ -436,17 +429,17 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     a.nc = ctx->nc;
     a.nt = nt;
     int n_chunks;
-    if (s.ngp <= MAXN) {
+    if (s.ngp <= 2 * MAXHALF) {
         n_chunks = 1;
         a.n_tile = s.ngp;
         a.src_from_b = 1;
     } else {
-        n_chunks = (s.ngp + MAXN - 1) / MAXN;
+        n_chunks = (s.ngp + 2 * MAXHALF - 1) / (2 * MAXHALF);
         a.n_tile = ((s.ngp + n_chunks - 1) / n_chunks + 15) / 16 * 16;
         a.src_from_b = 0;
     }
     a.n_gb = (ng + GBLK - 1) / GBLK;
-    a.kstages = (int)(s.kp / KS);
+    a.kstages = (int)(s.kp / KSTEP);
     a.acc_off = a.n_tile <= 128 ? 128u : 256u;
     a.tmem_cols = 2u * a.acc_off;
     a.wld = s.kp / 2;
@@ -460,16 +453,14 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     a.status = d_status;
     a.wait_limit = ctx->wait_limit;
     a.withhold = ctx->withhold_copies;
-    if (a.n_tile > MAXN || a.n_tile < 16) return cudaErrorNotSupported;
+    if (a.n_tile > 2 * MAXHALF || a.n_tile < 16) return cudaErrorNotSupported;
 
-    // ring: as many stages as fit in shared memory, 4 to MAXSTAGE
-    const uint32_t bbytes = (uint32_t)a.n_tile * RB;
-    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * GBLK * RB;
-    a.stage_bytes = (NPIECE * bbytes + sbytes + NPIECE * ATILE + WBYTES + 1023u) & ~1023u;
-    const size_t fixed = 1024 + (2 * NBAR + MAXSTAGE + 5) * sizeof(uint64_t) + 16;
-    a.nstage = (int)std::min<size_t>(MAXSTAGE, (SMEM_LIMIT - fixed) / a.stage_bytes);
-    if (a.nstage < 4) return cudaErrorNotSupported;
-    const size_t smem = fixed + (size_t)a.nstage * a.stage_bytes;
+    const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;
+    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * GBLK * ROWB;
+    const size_t stage_bytes = NPIECE * bbytes + sbytes + NPIECE * ATILE;
+    const size_t smem = 1024 + NSTAGE * stage_bytes + NSTAGE * (KSTEP / 2) * sizeof(float2) +
+                        (5 * NSTAGE + 5) * sizeof(uint64_t) + 16;
+    if (smem > SMEM_LIMIT) return cudaErrorNotSupported;
 
     // W table for this q (FP64 dE and w -+ dE, stored FP32)
     cudaError_t e = s.wtab.ensure((size_t)s.nw * (s.kp / 2) * sizeof(float2));
@@ -491,10 +482,10 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
 
     unsigned char* p0 = reinterpret_cast<unsigned char*>(s.rho.p);
     const size_t plane = (size_t)s.ngp * s.kp * 2;
-    CUtensorMap mb[NPIECE], ms[NPIECE];
-    for (int i = 0; i < NPIECE; ++i)
-        if (!qcx_make_bf16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile, KS) ||
-            !qcx_make_bf16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK, KS))
+    CUtensorMap mb[3], ms[3];
+    for (int i = 0; i < 3; ++i)
+        if (!qcx_make_bf16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile, KSTEP) ||
+            !qcx_make_bf16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK, KSTEP))
             return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute((const void*)k_chi0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
