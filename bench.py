@@ -35,6 +35,10 @@ sys.path.insert(0, ROOT)
 # of `bench.py --profile-case mid200` (dram__bytes_read.sum + dram__bytes_write.sum), and the commit of the kernel
 # source it was taken at; None once the kernel has changed since.
 CHI0_TRAFFIC = None
+# Executed FP32 flops of one k_pair_density_fused launch over 1 q of the mid workload (512 k x 181 G), from the
+# ncu thread-instruction counters of `bench.py --profile-case mid` (2 FFMA + FADD + FMUL,
+# smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), and the commit of the kernel source.
+PD_FP32_FLOPS = {"flops": 2 * 38126002176 + 7493828608 + 20906803200, "commit": "83a9631"}
 METRIC = "eps^-1 (q,w) blocks/s vs FP64 plain GPU path at <=1e-4 rel err; tensor-pipe %"
 WORKLOAD = ("mid: diamond a=5.43 A, 12 sp shells/atom (N_b=96), 8x8x8 k, N_v=4, N_c=32 (N_t=65536), "
             "N_G=181, 50 q x 200 w on 0-60 eV, eta=0.1 eV")
@@ -396,6 +400,14 @@ def run_ours(args, ws, rank, local):
                             "avg_launch_ms": chi_avg,
                             "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)"},
                "pair_density": {"kernel": "k_pair_density_fused", "avg_launch_ms": pd_avg, "bound": "alu",
+                                "fp32_flops_per_launch": PD_FP32_FLOPS["flops"],
+                                "fp32_flops_source": f"ncu FFMA/FADD/FMUL thread-instruction counts of one launch "
+                                                     f"(1 q), kernel at commit {PD_FP32_FLOPS['commit']}",
+                                "achieved_tflops": PD_FP32_FLOPS["flops"] / (pd_avg / 1e3) / 1e12,
+                                "fp32_peak_tflops": fma.get("fp32_tflops"),
+                                "frac": (PD_FP32_FLOPS["flops"] / (pd_avg / 1e3) / 1e12 / fma["fp32_tflops"]
+                                         if fma.get("fp32_tflops") else None),
+                                "peak_source": "FFMA microbenchmark measured in this run (libqcx_peaks)",
                                 "algorithmic_bytes": pd_bytes, "achieved_GBs": pd_bytes / (pd_avg / 1e3) / 1e9,
                                 "hbm_peak_GBs": peaks.get("hbm_gbs", 6800.0),
                                 "hbm_frac": pd_bytes / (pd_avg / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),

@@ -143,3 +143,103 @@ def bin_loss(qmag_bohr, L, edges_bohr):
     nz = cnt > 0
     out[nz] /= cnt[nz][:, None]
     return out, 0.5 * (np.asarray(edges_bohr[1:]) + np.asarray(edges_bohr[:-1])), cnt
+
+
+# --------------------------------------------------------------------------
+# General (relativistic) rate with a velocity flux and a vector or scalar
+# mediator: Eqs. (general_rate), (H), (cross_section_iso) and (v_min).
+# --------------------------------------------------------------------------
+CM2_S_TO_EV3 = (HBARC_EV_CM ** 2) * HBAR_EV_S      # 1 / (cm^2 s) in eV^3
+
+
+def shm_speed_distribution(v, v0, vesc, vE):
+    """Normalised speed distribution f(v) (int f dv = 1, speeds in units of c) of
+    the truncated Maxwellian f(v_vec) ~ exp(-|v_vec + v_E|^2/v0^2) Theta(vesc - |v_vec + v_E|):
+    f(v) = v^2 int dOmega f(v_vec), the angular integral done in closed form
+    (2 pi int_{-1}^{c_max} dc exp(-(v^2 + vE^2 + 2 v vE c)/v0^2), c_max the
+    escape-speed cut)."""
+    z = vesc / v0
+    norm = pi ** 1.5 * v0 ** 3 * (erf(z) - 2.0 / sqrt(pi) * z * exp(-z * z))
+    out = np.zeros(np.shape(v))
+    for i, vi in enumerate(np.atleast_1d(v)):
+        if vi <= 0.0:
+            continue
+        B = 2.0 * vi * vE / v0 ** 2
+        cmax = min(1.0, (vesc ** 2 - vi ** 2 - vE ** 2) / (2.0 * vi * vE))
+        if cmax < -1.0:
+            continue
+        A = (vi ** 2 + vE ** 2) / v0 ** 2
+        out[i] = 2.0 * pi * vi * vi / (norm * B) * (exp(-(A - B)) - exp(-(A + B * cmax)))
+    return out
+
+
+def h_mediator(E, Ep, q, m_chi, kind):
+    """H_A'(q) of Eq. (H): kind 0 vector, (E + E')^2 - q^2; kind 1 scalar, 4 m^2 - (E - E')^2 + q^2."""
+    if kind == 0:
+        return (E + Ep) ** 2 - q * q
+    return 4.0 * m_chi * m_chi - (E - Ep) ** 2 + q * q
+
+
+@dataclass
+class RelParams:
+    m_chi_eV: float = 1e9
+    sigma_e_cm2: float = 1e-39
+    m_med_eV: float = -1.0            # < 0: heavy mediator; 0: massless; > 0: that mass
+    mediator: int = 0                 # 0 vector, 1 scalar
+    rho_T_g_cm3: float = 2.329
+    w_gap_eV: float = 1.1
+    w_pp_eV: float = 3.75
+
+
+def mediator_factor(w, q, m_med):
+    """(m_A'^2 + (alpha m_e)^2)^2 / (w^2 - q^2 - m_A'^2)^2; 1 in the heavy limit (m_med < 0)."""
+    if m_med < 0:
+        return 1.0
+    return (m_med ** 2 + AME_EV ** 2) ** 2 / (w * w - q * q - m_med ** 2) ** 2
+
+
+def dR_dw_general(qbin_bohr, w_ha, L, v, dphidv, p: RelParams):
+    """dR/dw [events/(kg yr eV)] = (1/rho_T) int dv dPhi/dv dsigma/dw per target
+    mass, dsigma/dw of Eq. (cross_section_iso):
+      sigma_e/(16 pi mu^2) 1/(E (E - w)) int dq q H(q) F_med(w, q) S(w, q) Theta(v - v_min)/v^2,
+      S = q^2 L/(2 pi alpha),  E = gamma m_chi,  v_min = q/(2 gamma m_chi) + w/q (Eq. (v_min)).
+    v[nv] (units of c), dphidv[nv] (1/(cm^2 s) per unit v): trapezoid in v; the
+    q integral is the trapezoid over qbin (L = 0 outside).  Energy transfers
+    with E - w <= m_chi are kinematically closed and contribute 0."""
+    q = np.asarray(qbin_bohr, float) * AME_EV
+    w = np.asarray(w_ha, float) * HARTREE_EV
+    v = np.asarray(v, float)
+    flux = np.asarray(dphidv, float) * CM2_S_TO_EV3
+    m = p.m_chi_eV
+    mu = m * ME_EV / (m + ME_EV)
+    sigma = p.sigma_e_cm2 / HBARC_EV_CM ** 2
+    rho_T = p.rho_T_g_cm3 * EV_PER_GRAM * HBARC_EV_CM ** 3
+    out = np.zeros(w.shape[0])
+    for iw, wv in enumerate(w):
+        per_v = np.zeros(v.shape[0])
+        for ivel, vv in enumerate(v):
+            if vv <= 0.0 or vv >= 1.0:
+                continue
+            gam = 1.0 / sqrt(1.0 - vv * vv)
+            E = gam * m
+            Ep = E - wv
+            if Ep <= m:
+                continue
+            vmin = q / (2.0 * gam * m) + wv / q
+            S = q * q * np.asarray(L)[:, iw] / (2.0 * pi * ALPHA)
+            g = q * h_mediator(E, Ep, q, m, p.mediator) * mediator_factor(wv, q, p.m_med_eV) * S / (vv * vv)
+            g = np.where(vv >= vmin, g, 0.0)
+            per_v[ivel] = sigma / (16.0 * pi * mu * mu) / (E * Ep) * np.trapezoid(g, q)
+        out[iw] = np.trapezoid(flux * per_v, v) / rho_T
+    return natural_to_kg_yr(out)
+
+
+def reach(dRQ, sigma_ref_cm2, exposure_kg_yr, n_events=2.3):
+    """Cross section at which n_events are expected for exposure_kg_yr above each
+    ionisation threshold Q = 1..nQ (the rate is linear in sigma_e; zero
+    background): n_events sigma_ref / (exposure sum_{Q' >= Q} dR_Q'(sigma_ref))."""
+    tail = np.cumsum(np.asarray(dRQ, float)[::-1])[::-1]
+    out = np.full(tail.shape, np.inf)
+    nz = tail > 0
+    out[nz] = n_events * sigma_ref_cm2 / (exposure_kg_yr * tail[nz])
+    return out
