@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one k_chi0_tc launch over 1 q x 200 w of the mid workload, from one ncu capture
 # of `bench.py --profile-case mid200` (dram__bytes_read.sum + dram__bytes_write.sum), and the commit of the kernel
 # source it was taken at; None once the kernel has changed since.
-CHI0_TRAFFIC = None
+CHI0_TRAFFIC = {"bytes": 923402240 + 182239232, "commit": "debafdc"}
 # Executed FP32 flops of one k_pair_density_fused launch over 1 q of the mid workload (512 k x 181 G), from the
 # ncu thread-instruction counters of `bench.py --profile-case mid` (2 FFMA + FADD + FMUL,
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), and the commit of the kernel source.
@@ -381,8 +381,9 @@ def run_ours(args, ws, rank, local):
 
     if rank == 0:
         # per q: G setup, pair densities, W table, chi0, Gauss-Jordan, FP64 diagonal correction, loss by the
-        # quadratic form, |q+G|; per step two binnings and two rate + recoil pairs
-        launches_per_step = nq * 8 + 2 + 4
+        # quadratic form, |q+G|, the dielectric values kept for 3-D binning; per step two binnings and two rate +
+        # recoil pairs
+        launches_per_step = nq * 9 + 2 + 4
         out = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "bf16",

@@ -243,6 +243,82 @@ qcx_status qcx_rate(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const d
                     const double* L, const qcx_halo_params* params, double* out_dRdw, int nQ,
                     double* out_dRQ);
 
+/* ------------------------------------------------ rate end: 3-D tables */
+
+/* The composite dielectric function binned in three-dimensional momentum
+ * space (Section III, Eq. (e_comp)): for the listed q (their qcx_invert_eps
+ * tables, same frequency grid) every value eps(w, q+G) is taken as
+ * eps^LFE = 1/[eps^-1]_GG (Eq. (eps_LFE), with the imaginary part of
+ * [eps^-1]_GG the stored -L_LFE) where |q+G| <= q_lfe and as
+ * eps^noLFE = eps_GG (Eq. (eps_noLFE)) above it, and falls in shell
+ * floor(|q+G|/dq) (< nshell), polar cell floor(theta n_theta/pi) and azimuthal
+ * cell floor(phi n_phi/(2 pi)) with phi in [0, 2 pi) (edge values to the last
+ * cell).  Writes the bin means out_eps[nshell][n_theta][n_phi][nw] and the
+ * numbers of values out_count[nshell][n_theta][n_phi] (empty: 0).  With
+ * fill != 0 an empty bin lying between filled shells of the same angular cell
+ * takes the linear interpolation in |q| of the nearest filled shells on either
+ * side and its count is set to -1.  Lengths in bohr^-1; outputs host or device.
+ * Errors: QCX_ERR_STATE (a q without loss tables), QCX_ERR_ARG (sizes, grids
+ * that differ, dq <= 0), QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_bin_eps3d(qcx_ctx* ctx, int nsel, const int* iq_list, double q_lfe, int nshell, double dq,
+                         int n_theta, int n_phi, int fill, qcx_c64* out_eps, double* out_count);
+
+/* Screening of the loss function (Section IV.C): Im(-1/eps)_scr =
+ * Im eps / |eps_scr|^2 (Eq. (ELF_screening)) with eps_scr = eps itself
+ * (QCX_SCREEN_SELF: the loss function Im(-1/eps)), 1 (QCX_SCREEN_NONE), the
+ * modified Thomas-Fermi model (QCX_SCREEN_MTF, Eq. (MTF); eps0, tau, wp_eV,
+ * qtf_eV) or the Lindhard function of an electron gas of density ne_bohr3 with
+ * damping f_p (QCX_SCREEN_LINDHARD, Eq. (Lindhard); fp > 0). */
+#define QCX_SCREEN_SELF 0
+#define QCX_SCREEN_NONE 1
+#define QCX_SCREEN_MTF 2
+#define QCX_SCREEN_LINDHARD 3
+typedef struct {
+    int model;
+    double eps0, tau, wp_eV, qtf_eV;   /* modified Thomas-Fermi parameters */
+    double ne_bohr3, fp;               /* Lindhard: electron density (bohr^-3), damping fraction of w_p */
+} qcx_screening;
+
+/* Isotropic loss function of 3-D tables (as from qcx_bin_eps3d):
+ * out_L[nshell][nw] = mean over the angular cells of each shell with
+ * count != 0 of Im eps_cell / |eps_scr|^2, the screening models evaluated at
+ * the shell centre |q| = (s + 1/2) dq and at w[nw] (Hartree);
+ * out_ncell[nshell] = cells used (0: L = 0).  Inputs and outputs host or
+ * device.  Errors: QCX_ERR_ARG (sizes, unknown model, fp <= 0 for Lindhard),
+ * QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_loss_isotropic(qcx_ctx* ctx, int nshell, int n_theta, int n_phi, int nw, const double* w,
+                              double dq, const qcx_c64* eps, const double* count, const qcx_screening* scr,
+                              double* out_L, double* out_ncell);
+
+/* Particle and mediator of the general rate. */
+typedef struct {
+    double m_chi_eV;          /* dark-matter mass                                         */
+    double sigma_e_cm2;       /* reference cross section sigma_e                          */
+    double m_med_eV;          /* mediator mass: < 0 heavy limit, 0 massless, > 0 the mass */
+    int mediator;             /* 0 vector, 1 scalar (Eq. (H))                            */
+    double rho_T_g_cm3;       /* target mass density                                      */
+    double w_gap_eV, w_pp_eV; /* ionisation step model Q(w) = 1 + floor((w - w_gap)/w_pp) */
+    double exposure_kg_yr;    /* reach: exposure ...                                      */
+    double n_events;          /* ... and expected events (2.3: zero background, 90 % CL) */
+} qcx_rate_params;
+
+/* General rate for a velocity flux (Eqs. (general_rate), (H),
+ * (cross_section_iso), (v_min)): dR/dw = (1/rho_T) int dv dPhi/dv
+ * sigma_e/(16 pi mu^2) 1/(E (E - w)) int dq q H(q) F(w, q) S(w, q)
+ * Theta(v - v_min)/v^2 with S = q^2 L/(2 pi alpha), E = gamma m_chi,
+ * v_min = q/(2 gamma m_chi) + w/q and F = (m^2 + (alpha m_e)^2)^2/(w^2 - q^2 - m^2)^2
+ * (1 in the heavy limit); transfers with E - w <= m_chi contribute 0.
+ * qbin[nqbin] (bohr^-1, ascending) and L[nqbin][nw], w[nw] (Hartree, uniform),
+ * v[nv] (units of c, ascending) with dphidv[nv] (1/(cm^2 s) per unit v); both
+ * integrals by the composite trapezoid, accumulation in FP64.  Writes
+ * out_dRdw[nw] (events/(kg yr eV)), out_dRQ[nQ] (events/(kg yr) per
+ * ionisation step, Eq. (excitation_rate)) and, if not NULL, out_reach[nQ]:
+ * the cross section at which n_events are expected above threshold Q in the
+ * exposure.  Errors: QCX_ERR_ARG. */
+qcx_status qcx_rate_general(qcx_ctx* ctx, int nqbin, const double* qbin, int nw, const double* w, const double* L,
+                            int nv, const double* v, const double* dphidv, const qcx_rate_params* params,
+                            double* out_dRdw, int nQ, double* out_dRQ, double* out_reach);
+
 /* --------------------------------------------------- batched instances */
 
 /* Uneven (q, w) instances in one call: instance i is the frequency

@@ -423,6 +423,15 @@ qcx_status qcx_invert_eps(qcx_ctx* ctx, int iq, qcx_precision prec, qcx_c64* out
     CUDA_OR_FAIL(lt->qmag.ensure(ng * sizeof(double)), "alloc");
     k_kmag<<<(ng + 127) / 128, 128, 0, ctx->stream>>>(ng, s.kappa.as<double>(), lt->qmag.as<double>());
     CUDA_OR_FAIL(qcx_launch_invert(ctx, s, prec, lt->L.as<double>()), "invert kernel");
+    // the dielectric values of this q kept for the 3-D binning of the composite function
+    CUDA_OR_FAIL(lt->eps.ensure(2 * (size_t)nw * ng * sizeof(double2)), "alloc eps table");
+    CUDA_OR_FAIL(lt->kvec.ensure(3 * sizeof(double) * ng), "alloc");
+    CUDA_OR_FAIL(qcx_launch_store_eps(ctx->stream, nw, ng, s.diag_inv.as<double2>(), s.eps_diag.as<double2>(),
+                                      lt->L.as<double>(), lt->eps.as<double2>()),
+                 "store eps");
+    CUDA_OR_FAIL(cudaMemcpyAsync(lt->kvec.p, s.kappa.p, 3 * sizeof(double) * ng, cudaMemcpyDeviceToDevice,
+                                 ctx->stream),
+                 "copy q+G");
     lt->w.resize(nw);
     CUDA_OR_FAIL(cudaMemcpyAsync(lt->w.data(), s.w.p, nw * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "w");
     lt->valid = true;

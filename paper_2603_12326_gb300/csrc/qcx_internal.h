@@ -68,6 +68,8 @@ struct LossTab {
     int ng = 0, nw = 0;
     DevBuf L;                  // [2][nw][ng] double: LFE then noLFE
     DevBuf qmag;               // [ng] double |q+G|
+    DevBuf eps;                // [2][nw][ng] double2: eps^LFE (from Re [eps^-1]_GG and -L_LFE), eps^noLFE = eps_GG
+    DevBuf kvec;               // [ng][3] double q + G (bohr^-1)
     std::vector<double> w;     // frequency grid (host copy, to check consistency)
 };
 
@@ -216,6 +218,11 @@ cudaError_t qcx_launch_bin(qcx_ctx* ctx, int nsel, const double* const* d_L, con
 cudaError_t qcx_launch_rate(qcx_ctx* ctx, int nqbin, const double* d_q, int nw, const double* d_w,
                             const double* d_L, const qcx_halo_params& p, double* d_dRdw, int nQ,
                             double* d_dRQ);
+cudaError_t qcx_launch_recoil(cudaStream_t st, int nw, const double* d_w, const double* d_dRdw, double wgap_eV,
+                              double wpp_eV, int nQ, double* d_dRQ);
+// rate_ext.cu: the per-q dielectric values kept for the 3-D binning (after qcx_launch_invert)
+cudaError_t qcx_launch_store_eps(cudaStream_t st, int nw, int ng, const double2* diag_inv, const double2* eps_diag,
+                                 const double* L_lfe, double2* out);
 
 // 4 pi as used by v^1/2 = sqrt(4 pi)/|k|
 #define QCX_SQRT_4PI 3.5449077018110318

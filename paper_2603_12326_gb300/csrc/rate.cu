@@ -110,6 +110,12 @@ cudaError_t qcx_launch_bin(qcx_ctx* ctx, int nsel, const double* const* d_L, con
     return cudaGetLastError();
 }
 
+cudaError_t qcx_launch_recoil(cudaStream_t st, int nw, const double* d_w, const double* d_dRdw, double wgap_eV,
+                              double wpp_eV, int nQ, double* d_dRQ) {
+    k_recoil<<<(nQ + 63) / 64, 64, 0, st>>>(nw, d_w, d_dRdw, wgap_eV, wpp_eV, nQ, d_dRQ);
+    return cudaGetLastError();
+}
+
 cudaError_t qcx_launch_rate(qcx_ctx* ctx, int nqbin, const double* d_q, int nw, const double* d_w,
                             const double* d_L, const qcx_halo_params& p, double* d_dRdw, int nQ,
                             double* d_dRQ) {

@@ -37,6 +37,32 @@ def halo_params(m_chi_eV=1e9, sigma_e_cm2=1e-39, rho_chi_GeV_cm3=0.3, v0_kms=238
                       w_gap_eV, w_pp_eV)
 
 
+class Screening(ct.Structure):
+    """qcx_screening."""
+    _fields_ = [("model", ct.c_int), ("eps0", ct.c_double), ("tau", ct.c_double), ("wp_eV", ct.c_double),
+                ("qtf_eV", ct.c_double), ("ne_bohr3", ct.c_double), ("fp", ct.c_double)]
+
+
+SCREEN_SELF, SCREEN_NONE, SCREEN_MTF, SCREEN_LINDHARD = 0, 1, 2, 3
+
+
+def screening(model=SCREEN_SELF, eps0=11.3, tau=1.563, wp_eV=16.6, qtf_eV=4130.0, ne_bohr3=0.0, fp=0.1):
+    return Screening(model, eps0, tau, wp_eV, qtf_eV, ne_bohr3, fp)
+
+
+class RateParams(ct.Structure):
+    """qcx_rate_params."""
+    _fields_ = [("m_chi_eV", ct.c_double), ("sigma_e_cm2", ct.c_double), ("m_med_eV", ct.c_double),
+                ("mediator", ct.c_int), ("rho_T_g_cm3", ct.c_double), ("w_gap_eV", ct.c_double),
+                ("w_pp_eV", ct.c_double), ("exposure_kg_yr", ct.c_double), ("n_events", ct.c_double)]
+
+
+def rate_params(m_chi_eV=1e9, sigma_e_cm2=1e-39, m_med_eV=-1.0, mediator=0, rho_T_g_cm3=2.329, w_gap_eV=1.1,
+                w_pp_eV=3.75, exposure_kg_yr=1.0, n_events=2.3):
+    return RateParams(m_chi_eV, sigma_e_cm2, m_med_eV, mediator, rho_T_g_cm3, w_gap_eV, w_pp_eV, exposure_kg_yr,
+                      n_events)
+
+
 _SIGS = {
     "qcx_create": (I, [ct.POINTER(P), I, P]),
     "qcx_destroy": (None, [P]),
@@ -55,6 +81,9 @@ _SIGS = {
     "qcx_loss_function": (I, [P, I, P, P]),
     "qcx_bin_loss": (I, [P, I, P, I, I, P, P, P]),
     "qcx_rate": (I, [P, I, P, I, P, P, ct.POINTER(HaloParams), P, I, P]),
+    "qcx_bin_eps3d": (I, [P, I, P, D, I, D, I, I, I, P, P]),
+    "qcx_loss_isotropic": (I, [P, I, I, I, I, P, D, P, P, ct.POINTER(Screening), P, P]),
+    "qcx_rate_general": (I, [P, I, P, I, P, P, I, P, P, ct.POINTER(RateParams), P, I, P, P]),
     "qcx_solve_batch": (I, [P, I, P, P, P, D, I, P, P, P]),
     "qcx_batch_info": (I, [P, I, P]),
     "qcx_batch_autotune": (I, [P, I]),
@@ -270,6 +299,38 @@ class Context:
         self._check(qcx_rate(self.h, len(qbin), qa.ptr, len(w), wa.ptr, La.ptr, ct.byref(params),
                              P(dR.ctypes.data), nQ, P(dQ.ctypes.data) if nQ else None))
         return dR, dQ[:nQ]
+
+    # ------------------------------------------------ rate end: 3-D tables
+    def bin_eps3d(self, iq_list, q_lfe, nshell, dq, n_theta, n_phi, nw, fill=True):
+        """Composite eps binned in (|q|, theta, phi): (eps [nshell][nth][nph][nw], count [nshell][nth][nph])."""
+        iq = np.ascontiguousarray(iq_list, np.int32)
+        eps = np.zeros((nshell, n_theta, n_phi, nw), np.complex128)
+        cnt = np.zeros((nshell, n_theta, n_phi), np.float64)
+        self._check(qcx_bin_eps3d(self.h, len(iq), P(iq.ctypes.data), float(q_lfe), nshell, float(dq), n_theta,
+                                  n_phi, 1 if fill else 0, P(eps.ctypes.data), P(cnt.ctypes.data)))
+        return eps, cnt
+
+    def loss_isotropic(self, eps, count, w, dq, scr: Screening):
+        """Isotropic loss [nshell][nw] of 3-D tables and the cells used per shell."""
+        nshell, nth, nph, nw = eps.shape
+        e, c, wa = _Arg(eps, np.complex128), _Arg(count, np.float64), _Arg(w, np.float64)
+        L = np.zeros((nshell, nw), np.float64)
+        nc = np.zeros(nshell, np.float64)
+        self._check(qcx_loss_isotropic(self.h, nshell, nth, nph, nw, wa.ptr, float(dq), e.ptr, c.ptr, ct.byref(scr),
+                                       P(L.ctypes.data), P(nc.ctypes.data)))
+        return L, nc
+
+    def rate_general(self, qbin, w, L, v, dphidv, params: RateParams, nQ=0, want_reach=False):
+        """(dR/dw [nw], dR_Q [nQ], reach [nQ] or None) of the general rate."""
+        qa, wa, La = _Arg(qbin, np.float64), _Arg(w, np.float64), _Arg(L, np.float64)
+        va, fa = _Arg(v, np.float64), _Arg(dphidv, np.float64)
+        dR = np.zeros(len(w), np.float64)
+        dQ = np.zeros(max(nQ, 1), np.float64)
+        rc = np.zeros(max(nQ, 1), np.float64) if want_reach else None
+        self._check(qcx_rate_general(self.h, len(qbin), qa.ptr, len(w), wa.ptr, La.ptr, len(v), va.ptr, fa.ptr,
+                                     ct.byref(params), P(dR.ctypes.data), nQ, P(dQ.ctypes.data) if nQ else None,
+                                     P(rc.ctypes.data) if want_reach else None))
+        return dR, dQ[:nQ], (rc[:nQ] if want_reach else None)
 
     # ------------------------------------------------- batched instances
     def solve_batch(self, inst_q, inst_w, inst_gmax, eta, prec=QCX_MIXED, out_lfe=None, out_nolfe=None,
