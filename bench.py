@@ -340,6 +340,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_ms = _barrier_max(ws, e0.elapsed_time(e1) / n_e2e)
 
+    # ------------------------------------------ rate end on the mixed tables of every q (rank 0)
+    rate_end = rate_end_leg(ctx, prob, w) if rank == 0 and ws == 1 else None
+
     # ------------------------------------ accuracy over every q: mixed vs the FP64 GPU path
     # The e2e step left the mixed loss tables of all q in the context; each q is then recomputed by the
     # FP64 path (pinned to the oracle at 1e-10) at eight frequencies.
@@ -429,6 +432,8 @@ def run_ours(args, ws, rank, local):
                "clocks": clocks}
         if accuracy:
             out["accuracy"] = accuracy
+        if rate_end:
+            out["rate_end"] = rate_end
         if cpu:
             out["cpu_baseline"] = cpu
         if batched:
@@ -439,6 +444,46 @@ def run_ours(args, ws, rank, local):
             out["surrogate"] = surro
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+def rate_end_leg(ctx, prob, w, q_lfe=8.0, dq=0.02, nth=9, nph=16, nshell=640):
+    """The composite function of the timed workload's 50 q (mixed tables, 200 w)
+    in the paper's 3-D bins (dq = 0.02 alpha m_e, 9 x 16 angular cells, q_LFE = 8
+    alpha m_e), filled, reduced to the isotropic loss under four screening
+    choices, and the general rate of the halo flux (vector and scalar heavy
+    mediators) with recoil spectrum and reach; wall-clock times of the calls
+    (host outputs, so copies included)."""
+    import synth
+    from paper_2603_12326_gb300 import qcx
+    nq, nw = prob.nq, len(w)
+    t = {}
+    t0 = time.perf_counter()
+    eps, cnt = ctx.bin_eps3d(list(range(nq)), q_lfe, nshell, dq, nth, nph, nw, fill=True)
+    t["bin_eps3d_ms"] = 1e3 * (time.perf_counter() - t0)
+    ne = 8.0 / prob.cell.volume
+    L = {}
+    for name, model in (("self", qcx.SCREEN_SELF), ("none", qcx.SCREEN_NONE), ("mtf", qcx.SCREEN_MTF),
+                        ("lindhard", qcx.SCREEN_LINDHARD)):
+        t0 = time.perf_counter()
+        L[name], ncell = ctx.loss_isotropic(eps, cnt, w, dq, qcx.screening(model, ne_bohr3=ne, fp=0.1))
+        t[f"loss_isotropic_{name}_ms"] = 1e3 * (time.perf_counter() - t0)
+    used = ncell > 0
+    qs = (np.arange(nshell) + 0.5)[used] * dq
+    v = np.linspace(1e-6, 3e-3, 2000)
+    flux = synth.halo_flux(v)
+    rates = {}
+    for name, kind in (("vector", 0), ("scalar", 1)):
+        t0 = time.perf_counter()
+        dR, dQ, reach = ctx.rate_general(qs, w, L["self"][used], v, flux, qcx.rate_params(mediator=kind), nQ=10,
+                                         want_reach=True)
+        t[f"rate_general_{name}_ms"] = 1e3 * (time.perf_counter() - t0)
+        rates[name] = {"recoil_spectrum_events_per_kg_yr": [float(x) for x in dQ],
+                       "reach_cm2_1kg_yr": [float(x) for x in reach]}
+    return {"bins": {"shells": nshell, "dq_bohr": dq, "n_theta": nth, "n_phi": nph, "q_lfe_bohr": q_lfe,
+                     "filled": int(np.sum(cnt > 0)), "interpolated": int(np.sum(cnt < 0)),
+                     "shells_used": int(used.sum())},
+            "times": t, "rates": rates,
+            "flux": "standard halo, m_chi = 1 GeV, 2000 speeds to 3e-3 c"}
 
 
 def fma_peaks(device):

@@ -350,3 +350,29 @@ def mlp_init(seed: int = 2024, layers=(6, 128, 128, 128, 2)) -> np.ndarray:
         parts.append(rng.standard_normal(o * i) / np.sqrt(i))
         parts.append(np.zeros(o))
     return np.concatenate(parts).astype(np.float32)
+
+
+def halo_flux(v, m_chi_eV=1e9, rho_chi_GeV_cm3=0.3, v0_kms=238.0, vesc_kms=544.0, vE_kms=250.2):
+    """Differential flux dPhi/dv (1/(cm^2 s) per unit v, v in units of c) of the
+    standard halo seen from the Earth: n_chi v f(v) with n_chi = rho_chi/m_chi and
+    f(v) the speed distribution of the truncated Maxwellian
+    exp(-|v + v_E|^2/v0^2) Theta(v_esc - |v + v_E|) (angles integrated in closed
+    form).  An input of the general rate (the halo term of its flux), not part
+    of the screening method."""
+    from math import erf, exp, pi, sqrt
+    c = 299792.458
+    v0, vesc, vE = v0_kms / c, vesc_kms / c, vE_kms / c
+    z = vesc / v0
+    norm = pi ** 1.5 * v0 ** 3 * (erf(z) - 2.0 / sqrt(pi) * z * exp(-z * z))
+    out = np.zeros(len(v))
+    for i, vi in enumerate(v):
+        if vi <= 0.0:
+            continue
+        cmax = min(1.0, (vesc * vesc - vi * vi - vE * vE) / (2.0 * vi * vE))
+        if cmax < -1.0:
+            continue
+        b = 2.0 * vi * vE / (v0 * v0)
+        a = (vi * vi + vE * vE) / (v0 * v0)
+        f = 2.0 * pi * vi * vi / (norm * b) * (exp(-(a - b)) - exp(-(a + b * cmax)))
+        out[i] = rho_chi_GeV_cm3 * 1e9 / m_chi_eV * vi * c * 1e5 * f
+    return out

@@ -166,3 +166,13 @@ def test_composite_binning_fill_and_isotropic_loss_by_hand():
     assert L2[0, 0] == pytest.approx(0.5 * (0.5 + 0.2), rel=1e-15)
     L3, _ = bins3d.isotropic_loss(two, np.ones((1, 1, 2)), eps_scr=np.ones((1, 1)))
     assert L3[0, 0] == pytest.approx(1.0, rel=1e-15)
+
+
+def test_synthetic_halo_flux_is_the_oracle_halo_flux():
+    """The benchmark's flux input (synth.halo_flux) is n_chi v f(v) with the
+    oracle's speed distribution."""
+    import synth
+    p, v0, vesc, vE = _shm()
+    v = np.linspace(1e-6, 3e-3, 501)
+    want = p.rho_chi_GeV_cm3 * 1e9 / p.m_chi_eV * v * rate.C_KM_S * 1e5 * rate.shm_speed_distribution(v, v0, vesc, vE)
+    assert np.allclose(synth.halo_flux(v), want, rtol=1e-13, atol=0)
