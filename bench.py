@@ -370,6 +370,9 @@ def run_ours(args, ws, rank, local):
     chi64_tflops = 8.0 * nt * ng * ng * nw64 / (chi64_ms / 1e3) / 1e12
     fma = fma_peaks(local)
 
+    # ------------------------------------ spectral route (binned spectral function + Kramers-Kronig)
+    spec = spectral_leg(ctx, prob, G, w, eta, stream, fma) if (rank == 0 and ws == 1 and not args.no_spectral) else None
+
     # ------------------------------------------- batched uneven instances (rank 0, N=1)
     batched = batched_leg(stream) if (rank == 0 and ws == 1) else None
     large = large_leg(stream) if (rank == 0 and ws == 1 and not args.no_large) else None
@@ -434,6 +437,8 @@ def run_ours(args, ws, rank, local):
             out["accuracy"] = accuracy
         if rate_end:
             out["rate_end"] = rate_end
+        if spec:
+            out["spectral"] = spec
         if cpu:
             out["cpu_baseline"] = cpu
         if batched:
@@ -506,6 +511,97 @@ def fma_peaks(device):
     out["method"] = ("8 independent FMA chains per thread, 4 CTAs of 256 threads per SM, best of 5 launches "
                      "timed with CUDA events")
     return out
+
+
+def _masked_err(a, b, frac=1e-3):
+    """Worst relative error of a against b per spectrum (fixed G, column of [w][G]) where
+    |b| exceeds frac of the spectrum's maximum."""
+    top = np.max(np.abs(b), axis=0, keepdims=True)
+    m = np.abs(b) > frac * top
+    return float(np.max(np.abs(a[m] - b[m]) / np.abs(b[m])))
+
+
+def spectral_leg(ctx, prob, G, w, eta, stream, fma, nq_spec=10, frac=20, nsample=8):
+    """The spectral route to chi0 (spectral function on a uniform energy grid of
+    step eta/frac, principal part by the Kramers-Kronig relations) on the first
+    nq_spec q of the timed workload, all 200 w: the mixed route timed per q with
+    CUDA events (pair densities, chi0, inverse), its contraction kernel's FP32
+    roofline from the stage times the library records, the FP64 route on q 0,
+    and the loss of both routes against the FP64 direct sum at nsample
+    frequencies of q 0 (the route's discretisation in energy, second order in
+    the step)."""
+    from paper_2603_12326_gb300 import QCX_FP64
+    nw, ng = len(w), prob.ng
+    step = eta / frac
+    grids = [ctx.spectral_grid(iq, step) for iq in range(nq_spec)]
+    ctx.pair_density(0, G, QCX_MIXED)                         # warm-up
+    ctx.chi0_spectral(0, w, eta, grids[0][0], step, grids[0][1], QCX_MIXED)
+    ctx.invert_eps(0, QCX_MIXED, want=False)
+    torch.cuda.synchronize()
+    kk_ms, wt_ms, flops = [], [], 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for iq in range(nq_spec):
+        E0, nbin = grids[iq]
+        ctx.pair_density(iq, G, QCX_MIXED)
+        ctx.chi0_spectral(iq, w, eta, E0, step, nbin, QCX_MIXED)
+        tm = ctx.spectral_timings()
+        kk_ms.append(tm["contraction"])
+        wt_ms.append(tm["weights"])
+        flops += 4.0 * nw * nbin * ng * (ng + 1)             # 4 FMA per (w, grid point, G <= G') pair
+        ctx.invert_eps(iq, QCX_MIXED, want=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # q 0 again for its tables (the loop ended on the last q)
+    ctx.pair_density(0, G, QCX_MIXED)
+    ctx.chi0_spectral(0, w, eta, grids[0][0], step, grids[0][1], QCX_MIXED)
+    ctx.invert_eps(0, QCX_MIXED, want=False)
+    Lm = ctx.loss_function(0, QCX_MIXED)
+    # FP64 route, q 0
+    ctx.pair_density(0, G, QCX_FP64)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    ctx.chi0_spectral(0, w, eta, grids[0][0], step, grids[0][1], QCX_FP64)
+    ctx.invert_eps(0, QCX_FP64, want=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    tm64 = ctx.spectral_timings()
+    L64 = ctx.loss_function(0, QCX_FP64)
+    # the direct sum in FP64 at nsample frequencies of q 0
+    sample = np.linspace(1, nw - 1, nsample).astype(int)
+    ctx.chi0(0, w[sample], eta, QCX_FP64)
+    ctx.invert_eps(0, QCX_FP64, want=False)
+    Ld = ctx.loss_function(0, QCX_FP64)
+    kk = float(np.sum(kk_ms))
+    achieved = flops / (kk / 1e3) / 1e12
+    flops64 = 4.0 * nw * grids[0][1] * ng * (ng + 1)
+    ach64 = flops64 / (tm64["contraction"] / 1e3) / 1e12
+    return {"workload": f"first {nq_spec} q of the timed workload x {nw} w, grid step eta/{frac} "
+                        f"({grids[0][1]} points at q 0)",
+            "value": nq_spec * nw / (ms / 1e3), "unit": "blocks/s",
+            "ms_per_q": ms / nq_spec,
+            "precision": "FP32 pair densities, weights and contraction (two-level sums, chunks added in FP64); "
+                         "grid and K in FP64; inverse as the mixed direct path",
+            "contraction": {"kernel": "k_spec_kk<float>", "bound": "alu", "ms_per_q": kk / nq_spec,
+                            "weights_ms_per_q": float(np.sum(wt_ms)) / nq_spec,
+                            "flops": "4 FMA per (w, grid point, G <= G') pair",
+                            "achieved_tflops": achieved, "peak_tflops": fma.get("fp32_tflops"),
+                            "frac": achieved / fma["fp32_tflops"] if fma.get("fp32_tflops") else None,
+                            "peak_source": "FFMA microbenchmark measured in this run (libqcx_peaks)"},
+            "fp64": {"value": nw / (ms64 / 1e3), "unit": "blocks/s", "sample": "q 0 (chi0 + inverse; pair "
+                     "densities excluded)", "contraction_ms": tm64["contraction"], "weights_ms": tm64["weights"],
+                     "contraction_tflops": ach64,
+                     "frac_of_fp64_peak": ach64 / fma["fp64_tflops"] if fma.get("fp64_tflops") else None},
+            "vs_direct_sum": {"mixed_L_lfe": _masked_err(Lm[0][sample], Ld[0]),
+                              "mixed_L_nolfe": _masked_err(Lm[1][sample], Ld[1]),
+                              "fp64_L_lfe": _masked_err(L64[0][sample], Ld[0]),
+                              "fp64_L_nolfe": _masked_err(L64[1][sample], Ld[1]),
+                              "mixed_vs_fp64_route_L_lfe": _masked_err(Lm[0], L64[0]),
+                              "sample": f"q 0, {nsample} w, every G; per spectrum where L > 1e-3 of its maximum "
+                                        f"over the sampled w"}}
 
 
 def accuracy_sweep(ctx, prob, G, w, eta, outL, nsample=8):
@@ -792,6 +888,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-correction leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the accuracy sweep over every q")
     ap.add_argument("--no-large", action="store_true", help="skip the large-workload leg")
+    ap.add_argument("--no-spectral", action="store_true", help="skip the spectral-route leg")
     ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "mid200", "batch", "mlp"],
                     help="small case for profilers, no report: mid = 1 q x 50 w of the mid workload, 2 passes; "
                          "batch = the uneven workload once; mlp = one gradient and one prediction")

@@ -172,6 +172,57 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
 qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, qcx_precision prec,
                     qcx_c64* out_chi0);
 
+/* The spectral route to the same chi0 (Eq. (eRPA_spectral): the spectral
+ * part of Eq. (RPA), with the principal part from the Kramers-Kronig
+ * relations, Section II.D and its footnote).  On the uniform grid
+ * E_b = E0 + b step (b = 0 .. nbin-1, Hartree) each transition's delta is
+ * shared between its two neighbouring grid points with hat weights
+ * (dE_t = E_b + x step, 0 <= x < 1: weight 1 - x to b, x to b + 1), giving the
+ * spectral weights
+ *   S_b[G][G'] = 2/(N_k V) sum_t phi_b(dE_t) conj(rho_t(G)) rho_t(G'),
+ * formed once per q; then
+ *   chi0(w) = sum_b S_b [1/(w - E_b + i eta) - 1/(w + E_b + i eta)]
+ * (the same retarded broadening as qcx_chi0, so both routes agree exactly
+ * when every dE_t lies on the grid and otherwise differ by the interpolation
+ * in energy, second order in step) and eps = 1 - v^1/2 chi0 v^1/2 kept in the
+ * context like qcx_chi0, for qcx_invert_eps.  Needs qcx_pair_density(iq) in
+ * the same precision.  QCX_FP64: FP64 throughout.  QCX_MIXED: FP32 pair
+ * densities (the mixed path's), FP32 spectral weights, FP32 contraction summed
+ * in two levels (partial sums over 64 grid points, chunks of at most 4096
+ * points added in FP64); grid and K in FP64.
+ *   out_chi0[nw][ng][ng]  optional, row G, column G' (complex double)
+ *   out_S[nbin][ng][ng]   optional spectral weights (complex double); large
+ * Memory: the weights are formed in chunks of grid points (about 4 GiB, or
+ * qcx_set_spectral_chunk), plus [ng][nt] grouped pair densities.
+ * Errors: QCX_ERR_STATE, QCX_ERR_ARG (nw < 1, eta <= 0, step <= 0, nbin < 2,
+ * non-finite w or E0, a dE_t outside [E0, E0 + (nbin - 1) step)),
+ * QCX_ERR_UNSUPPORTED (more than 2^31 - 1 transitions), QCX_ERR_ALLOC,
+ * QCX_ERR_CUDA. */
+qcx_status qcx_chi0_spectral(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, double E0,
+                             double step, int nbin, qcx_precision prec, qcx_c64* out_chi0,
+                             qcx_c64* out_S);
+
+/* The grid that qcx_chi0_spectral needs for q number iq at spacing step:
+ * E0 = step floor(min dE / step) - step, nbin = floor((max dE - E0)/step) + 3,
+ * so every transition lies inside with one spare point on each side.
+ * Errors: QCX_ERR_STATE (no states), QCX_ERR_ARG (step <= 0, non-finite
+ * energies, more than 2^30 points), QCX_ERR_CUDA. */
+qcx_status qcx_spectral_grid(qcx_ctx* ctx, int iq, double step, double* E0, int* nbin);
+
+/* Grid points per chunk of qcx_chi0_spectral (rounded down to a multiple of
+ * 32, at least 32); 0 (default) takes them from a 4 GiB budget for the
+ * chunk's spectral weights.  Results do not depend on it beyond rounding
+ * (chunks are added in FP64).  Errors: QCX_ERR_ARG (ctx NULL, bins < 0). */
+qcx_status qcx_set_spectral_chunk(qcx_ctx* ctx, int bins);
+
+/* Device times (ms, CUDA events on the context's stream) of the stages of the
+ * last qcx_chi0_spectral call: ms[0] grouping of the transitions by grid
+ * point, ms[1] gather of the pair densities and the K table, ms[2] spectral
+ * weights, ms[3] Kramers-Kronig contraction, ms[4] Dyson step (zeros before
+ * the first call).  Library plumbing, no counterpart in the paper.
+ * Errors: QCX_ERR_ARG (ctx or ms NULL). */
+qcx_status qcx_spectral_timings(qcx_ctx* ctx, double* ms);
+
 /* Inverse of every eps(w) of the last qcx_chi0(iq) call: Gauss-Jordan with
  * partial pivoting (FP64; for QCX_MIXED FP32 followed, where the block is
  * ill-conditioned, by one FP64 residual correction of the diagonal).

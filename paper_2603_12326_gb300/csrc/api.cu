@@ -50,33 +50,10 @@ inline int nblocks(size_t n, int t = 256) {
     return (int)(b > 4096 ? 4096 : (b ? b : 1));
 }
 
-#define CUDA_OR_FAIL(call, what)                                                                \
-    do {                                                                                        \
-        cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess) {                                                                \
-            cudaGetLastError();                                                                 \
-            return ctx->fail(e_ == cudaErrorMemoryAllocation ? QCX_ERR_ALLOC : QCX_ERR_CUDA,    \
-                             std::string(what) + ": " + cudaGetErrorString(e_));                \
-        }                                                                                       \
-    } while (0)
-
 bool finite_all(const double* p, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return false;
     return true;
-}
-
-// host copy of a small host-or-device array
-template <typename T> cudaError_t fetch(qcx_ctx* ctx, std::vector<T>& out, const T* src, size_t n) {
-    out.resize(n);
-    if (!n) return cudaSuccess;
-    if (qcx_is_device_ptr(src)) {
-        cudaError_t e = cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream);
-        if (e != cudaSuccess) return e;
-        return cudaStreamSynchronize(ctx->stream);
-    }
-    std::memcpy(out.data(), src, n * sizeof(T));
-    return cudaSuccess;
 }
 
 }  // namespace

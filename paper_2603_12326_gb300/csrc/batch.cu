@@ -39,16 +39,6 @@ constexpr int MAX_NG = 512;        // largest instance the solve kernels take
 constexpr int FT = 32, FK = 16;    // FP64 chi0 tile: 32 x 32 (G, G'), 16 transitions per stage
 constexpr int TC_KSTEP = 32;       // BF16 K elements per tensor-core pipeline stage
 
-#define CUDA_OR_FAIL(call, what)                                                                \
-    do {                                                                                        \
-        cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess) {                                                                \
-            cudaGetLastError();                                                                 \
-            return ctx->fail(e_ == cudaErrorMemoryAllocation ? QCX_ERR_ALLOC : QCX_ERR_CUDA,    \
-                             std::string(what) + ": " + cudaGetErrorString(e_));                \
-        }                                                                                       \
-    } while (0)
-
 // W[inst][t] = 1/(w - dE + i eta) - 1/(w + dE + i eta), dE = E_c(k+q) - E_v(k) in FP64; zero for padded t
 __global__ void k_weights_batch(int ninst, long long ld, long long nt, int nv, int nc, int nk, const double* Ek,
                                 const double* Ekq_all, const BatchInst* inst, double eta, float2* W) {
@@ -155,18 +145,6 @@ int sm_count(int device) {
         n = 0;
     }
     return n > 0 ? n : 1;
-}
-
-template <typename T> cudaError_t fetch(qcx_ctx* ctx, std::vector<T>& out, const T* src, size_t n) {
-    out.resize(n);
-    if (!n) return cudaSuccess;
-    if (qcx_is_device_ptr(src)) {
-        cudaError_t e = cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream);
-        if (e != cudaSuccess) return e;
-        return cudaStreamSynchronize(ctx->stream);
-    }
-    std::memcpy(out.data(), src, n * sizeof(T));
-    return cudaSuccess;
 }
 
 }  // namespace

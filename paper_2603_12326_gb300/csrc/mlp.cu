@@ -321,16 +321,6 @@ uint64_t splitmix64(uint64_t& s) {
     return z ^ (z >> 31);
 }
 
-#define CUDA_OR_FAIL(call, what)                                                                \
-    do {                                                                                        \
-        cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess) {                                                                \
-            cudaGetLastError();                                                                 \
-            return ctx->fail(e_ == cudaErrorMemoryAllocation ? QCX_ERR_ALLOC : QCX_ERR_CUDA,    \
-                             std::string(what) + ": " + cudaGetErrorString(e_));                \
-        }                                                                                       \
-    } while (0)
-
 }  // namespace
 
 struct MlpState {

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -106,6 +107,39 @@ struct BatchInst {
 #define QCX_BATCH_MAXQ 16      // distinct q per persistent tensor-core launch
 struct BatchPlan;
 void qcx_batch_destroy(BatchPlan* p);
+
+// Work space of the spectral route to chi0 (one q at a time, either precision).
+struct SpecBufs {
+    DevBuf bin, x;             // [nt] grid point and hat weight of each transition
+    DevBuf cnt, fill, off;     // per grid point: count, fill cursor, group offsets [nbin + 1]
+    DevBuf perm0, perm;        // [nt] transitions grouped by grid point (then ascending t)
+    DevBuf status, range;
+    DevBuf rhos, xs;           // pair densities [ng][nt] and x [nt] in the grouped order
+    DevBuf tp;                 // upper (G, G') tile pairs
+    DevBuf ktab;               // [nw][ldk] K(w, E_b)
+    DevBuf S;                  // spectral weights of one chunk of grid points
+    DevBuf chi;                // [nw][ng][ng] double2 chi0 accumulated over the chunks
+    DevBuf Sout;               // staging of exported weights
+    // stage times of the last call (CUDA events on the context's stream): grouping, gather and
+    // K table, spectral weights, contraction, Dyson step (ms)
+    std::vector<cudaEvent_t> ev;
+    double ms[5] = {0, 0, 0, 0, 0};
+    SpecBufs() = default;
+    SpecBufs(const SpecBufs&) = delete;
+    SpecBufs& operator=(const SpecBufs&) = delete;
+    ~SpecBufs() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    cudaError_t events(size_t n) {
+        while (ev.size() < n) {
+            cudaEvent_t e;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+            ev.push_back(e);
+        }
+        return cudaSuccess;
+    }
+};
 struct MlpState;
 void qcx_mlp_destroy(MlpState* m);
 
@@ -152,6 +186,8 @@ struct qcx_ctx {
     long long wait_limit = 4000000000LL;  // tensor-core kernels: clock cycles before a pipeline wait gives up
     int withhold_copies = 0;       // fault injection (tests): the per-q tensor-core kernel issues no copies
     MlpState* mlp = nullptr;       // surrogate network (parameters, Adam moments, work buffers)
+    SpecBufs spec;                 // spectral route work space
+    int spec_chunk_bins = 0;       // grid points per chunk of the spectral route (0: from a 4 GiB budget)
 
     ~qcx_ctx();
     qcx_status fail(qcx_status s, const std::string& msg) {
@@ -161,7 +197,33 @@ struct qcx_ctx {
 };
 
 // ------------------------------------------------------------ small utils
+// Return from a qcx_status function when a CUDA call fails: the last-error state is cleared
+// and `what` is recorded with CUDA's message in the context.
+#define CUDA_OR_FAIL(call, what)                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            cudaGetLastError();                                                                 \
+            return ctx->fail(e_ == cudaErrorMemoryAllocation ? QCX_ERR_ALLOC : QCX_ERR_CUDA,    \
+                             std::string(what) + ": " + cudaGetErrorString(e_));                \
+        }                                                                                       \
+    } while (0)
+
 bool qcx_is_device_ptr(const void* p);
+
+// Host copy of a small host-or-device array (device sources synchronise the stream).
+template <typename T> cudaError_t fetch(qcx_ctx* ctx, std::vector<T>& out, const T* src, size_t n) {
+    out.resize(n);
+    if (!n) return cudaSuccess;
+    if (qcx_is_device_ptr(src)) {
+        cudaError_t e = cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return e;
+        return cudaStreamSynchronize(ctx->stream);
+    }
+    std::memcpy(out.data(), src, n * sizeof(T));
+    return cudaSuccess;
+}
+
 // copy `bytes` from a host-or-device source into device memory (stream-ordered)
 cudaError_t qcx_copy_in(qcx_ctx* ctx, void* dst_dev, const void* src, size_t bytes);
 // copy device memory to a host-or-device destination; host destinations synchronise

@@ -269,29 +269,6 @@ cudaError_t qcx_launch_store_eps(cudaStream_t st, int nw, int ng, const double2*
 
 namespace {
 
-#define CUDA_OR_FAIL(call, what)                                                                \
-    do {                                                                                        \
-        cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess) {                                                                \
-            cudaGetLastError();                                                                 \
-            return ctx->fail(e_ == cudaErrorMemoryAllocation ? QCX_ERR_ALLOC : QCX_ERR_CUDA,    \
-                             std::string(what) + ": " + cudaGetErrorString(e_));                \
-        }                                                                                       \
-    } while (0)
-
-// host copy of a small host-or-device array
-template <typename T> cudaError_t fetch(qcx_ctx* ctx, std::vector<T>& out, const T* src, size_t n) {
-    out.resize(n);
-    if (!n) return cudaSuccess;
-    if (qcx_is_device_ptr(src)) {
-        cudaError_t e = cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream);
-        if (e != cudaSuccess) return e;
-        return cudaStreamSynchronize(ctx->stream);
-    }
-    std::memcpy(out.data(), src, n * sizeof(T));
-    return cudaSuccess;
-}
-
 inline int nblk(size_t n, int t) { return (int)((n + t - 1) / t); }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }

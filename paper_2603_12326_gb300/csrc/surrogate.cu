@@ -34,16 +34,6 @@ extern "C" qcx_status qcx_mlp_predict(qcx_ctx* ctx, int n, const float* X, float
 
 namespace {
 
-#define CUDA_OR_FAIL(call, what)                                                                \
-    do {                                                                                        \
-        cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess) {                                                                \
-            cudaGetLastError();                                                                 \
-            return ctx->fail(e_ == cudaErrorMemoryAllocation ? QCX_ERR_ALLOC : QCX_ERR_CUDA,    \
-                             std::string(what) + ": " + cudaGetErrorString(e_));                \
-        }                                                                                       \
-    } while (0)
-
 constexpr int HC_THREADS = 256;
 
 // chi0_00(w) for every frequency: one CTA per frequency, FP64 sum over t

@@ -74,6 +74,10 @@ _SIGS = {
     "qcx_set_states": (I, [P, I, P, I, P, P, I, P, I, P, P]),
     "qcx_pair_density": (I, [P, I, I, P, I, P]),
     "qcx_chi0": (I, [P, I, I, P, D, I, P]),
+    "qcx_chi0_spectral": (I, [P, I, I, P, D, D, D, I, I, P, P]),
+    "qcx_spectral_grid": (I, [P, I, D, ct.POINTER(D), ct.POINTER(I)]),
+    "qcx_set_spectral_chunk": (I, [P, I]),
+    "qcx_spectral_timings": (I, [P, P]),
     "qcx_invert_eps": (I, [P, I, I, P, P, P]),
     "qcx_set_refine_threshold": (I, [P, D]),
     "qcx_set_wait_limit": (I, [P, ct.c_longlong]),
@@ -253,6 +257,37 @@ class Context:
         oa = _Arg(o, np.complex128)
         self._check(qcx_chi0(self.h, iq, nw, wa.ptr, float(eta), prec, oa.ptr))
         return o
+
+    def chi0_spectral(self, iq, w, eta, E0, step, nbin, prec=QCX_FP64, want=False, want_S=False, out=None):
+        """qcx_chi0_spectral; returns chi0 [nw][ng][ng] (if wanted) and the spectral weights
+        [nbin][ng][ng] (if wanted)."""
+        wa = _Arg(w, np.float64)
+        nw = len(w)
+        self._nw[prec] = nw
+        ng = self._ng.get(prec, 0)
+        o = _out((nw, ng, ng), np.complex128, out) if (want or out is not None) else None
+        oa = _Arg(o, np.complex128)
+        S = np.zeros((int(nbin), ng, ng), np.complex128) if want_S else None
+        sa = _Arg(S, np.complex128)
+        self._check(qcx_chi0_spectral(self.h, iq, nw, wa.ptr, float(eta), float(E0), float(step), int(nbin), prec,
+                                      oa.ptr, sa.ptr))
+        return o, S
+
+    def spectral_grid(self, iq, step):
+        """(E0, nbin) of qcx_spectral_grid."""
+        e0, nb = ct.c_double(0.0), ct.c_int(0)
+        self._check(qcx_spectral_grid(self.h, iq, float(step), ct.byref(e0), ct.byref(nb)))
+        return e0.value, nb.value
+
+    def set_spectral_chunk(self, bins):
+        self._check(qcx_set_spectral_chunk(self.h, int(bins)))
+
+    def spectral_timings(self):
+        """Stage times (ms) of the last chi0_spectral call: grouping, gather + K table,
+        spectral weights, contraction, Dyson step."""
+        ms = np.zeros(5, np.float64)
+        self._check(qcx_spectral_timings(self.h, P(ms.ctypes.data)))
+        return dict(zip(("grouping", "gather", "weights", "contraction", "dyson"), ms.tolist()))
 
     def invert_eps(self, iq, prec=QCX_FP64, want=True):
         nw, ng = self._nw[prec], self._ng[prec]

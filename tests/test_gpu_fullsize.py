@@ -9,9 +9,9 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import rpa
+from oracle import rpa, spectral
 from paper_2603_12326_gb300 import QCX_FP64, QCX_MIXED
-from tests.gpu_util import context, rel, set_oracle_states
+from tests.gpu_util import context, rel, rel_spectrum, set_oracle_states
 
 pytestmark = pytest.mark.gpu
 SAMPLE_W = [40, 80, 120, 160]
@@ -89,3 +89,40 @@ def test_mid_workload_every_q_mixed_vs_fp64_gpu():
     ctx.close()
     print("mid workload, 50 q x 8 w, mixed vs FP64 GPU:", {k: f"{v:.2e}" for k, v in worst.items()})
     assert worst["L_lfe"] < 1e-4 and worst["L_nolfe"] < 1e-4
+
+
+def test_mid_workload_spectral_route(mid):
+    """The spectral route at the benchmark's size: q = 0 of the mid workload,
+    all 200 w, grid step eta/20 (about 8000 grid points, one chunk).  FP64
+    against the oracle's spectral route on a sampled 12 x 12 block of (G, G')
+    (the weights of a block need only its columns of rho) at 1e-10; the mixed
+    route against the FP64 route at the mixed bars (chi0 5e-5, loss 1e-4 per
+    spectrum where L > 1e-3 of its maximum)."""
+    p, Ck, Ckq, o = mid
+    step = p.eta / 20
+    dE = o["dE"]
+    E0 = step * np.floor(dE.min() / step) - step
+    nbin = int(np.floor((dE.max() - E0) / step)) + 3
+    ng = p.G_int.shape[0]
+    cols = np.unique(np.linspace(0, ng - 1, 12).astype(int))
+    S_sub = spectral.spectral_weights(o["rho"][:, cols], dE, E0, step, nbin, p.nk, p.cell.volume)
+    chi_sub = spectral.chi0_from_spectral(S_sub, E0, step, p.w, p.eta)
+    ctx = context()
+    set_oracle_states(ctx, p, [0], Ck, [Ckq])
+    assert ctx.spectral_grid(0, step) == (E0, nbin)
+    ctx.pair_density(0, p.G_int, QCX_FP64)
+    chi64, _ = ctx.chi0_spectral(0, p.w, p.eta, E0, step, nbin, QCX_FP64, want=True)
+    ctx.invert_eps(0, QCX_FP64, want=False)
+    L64 = ctx.loss_function(0, QCX_FP64)
+    ctx.pair_density(0, p.G_int, QCX_MIXED)
+    chim, _ = ctx.chi0_spectral(0, p.w, p.eta, E0, step, nbin, QCX_MIXED, want=True)
+    ctx.invert_eps(0, QCX_MIXED, want=False)
+    Lm = ctx.loss_function(0, QCX_MIXED)
+    ctx.close()
+    e64 = rel(chi64[:, cols][:, :, cols], chi_sub)
+    em = rel(chim, chi64), rel_spectrum(Lm[0], L64[0]), rel_spectrum(Lm[1], L64[1])
+    dd = rel_spectrum(L64[0][SAMPLE_W], o["L_lfe"])
+    print(f"mid spectral route ({nbin} points): FP64 vs oracle {e64:.2e}; mixed vs FP64 chi0 {em[0]:.2e}, "
+          f"L_LFE {em[1]:.2e}, L_noLFE {em[2]:.2e}; L_LFE vs the direct sum {dd:.2e}")
+    assert e64 < 1e-10
+    assert em[0] < 5e-5 and em[1] < 1e-4 and em[2] < 1e-4
