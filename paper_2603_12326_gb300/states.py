@@ -33,3 +33,15 @@ def load_problem(ctx, prob, iq_list=None):
         Ckq[j] = orthonormalise(ctx.overlap(prob.kpts + prob.qpts[iq][None, :]), prob.zkq(iq))
     ctx.set_states(prob.kpts, Ck, prob.Ek, prob.qpts[iq_list], Ckq, prob.Ekq[iq_list])
     return Ck, Ckq
+
+
+def load_optical(ctx, prob):
+    """Basis and states of an optical-limit problem (a single q = 0): valence and
+    conduction coefficients at the same k orthonormalised together, C = L^{-H} Q for
+    [Z_v | Z_c] split by columns.  Returns (C_v, C_c)."""
+    c, b = prob.cell, prob.basis
+    ctx.set_basis(c.lattice, c.atoms, b.shell_atom, b.shell_l, b.shell_exp)
+    C = orthonormalise(ctx.overlap(prob.kpts), np.concatenate([prob.Zk, prob.zkq(0)], axis=2))
+    Cv, Cc = np.ascontiguousarray(C[:, :, :prob.nv]), np.ascontiguousarray(C[:, :, prob.nv:])
+    ctx.set_states(prob.kpts, Cv, prob.Ek, prob.qpts[:1], Cc[None], prob.Ekq[:1])
+    return Cv, Cc

@@ -324,6 +324,22 @@ def truncate(p: Problem, nq, nw) -> Problem:
     return p
 
 
+def make_optical(base: str = "small", nw: int | None = None) -> Problem:
+    """The optical limit q -> 0 on the cell, basis, k grid, valence draws, energies
+    at k and G set of the small (or mid) workload: a single q = 0 whose conduction
+    draws and energies are seeded apart from the finite-q ones.  Its conduction
+    states live at k itself, so the consumer orthonormalises them together with
+    the valence draws (extra["joint"]), as eigenvectors of one H(k) would be."""
+    p = make_small() if base == "small" else make_mid()
+    rng = np.random.default_rng([p.seed, 999])
+    p.name = f"optical-{base}"
+    p.qpts = np.zeros((1, 3))
+    p.q_index = np.array([999])
+    p.Ekq = band_energies(rng, (1, p.nk, p.nc), 1.1, 30.0)
+    p.extra["joint"] = True
+    return truncate(p, None, nw)
+
+
 def make_tiny(seed: int = 7, shells_per_atom: int = 2, n_k: int = 2, nv: int = 2, nc: int = 3,
               ng: int = 9, nq: int = 2, nw: int = 16, lo: float = 0.3, hi: float = 2.0) -> Problem:
     """A tiny cell for brute-force checks (moderate exponents so that real-space
