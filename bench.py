@@ -372,6 +372,7 @@ def run_ours(args, ws, rank, local):
 
     # ------------------------------------ spectral route (binned spectral function + Kramers-Kronig)
     spec = spectral_leg(ctx, prob, G, w, eta, stream, fma) if (rank == 0 and ws == 1 and not args.no_spectral) else None
+    optic = optical_leg(stream) if (rank == 0 and ws == 1 and not args.no_spectral) else None
 
     # ------------------------------------------- batched uneven instances (rank 0, N=1)
     batched = batched_leg(stream) if (rank == 0 and ws == 1) else None
@@ -439,6 +440,8 @@ def run_ours(args, ws, rank, local):
             out["rate_end"] = rate_end
         if spec:
             out["spectral"] = spec
+        if optic:
+            out["optical_limit"] = optic
         if cpu:
             out["cpu_baseline"] = cpu
         if batched:
@@ -530,7 +533,8 @@ def spectral_leg(ctx, prob, G, w, eta, stream, fma, nq_spec=10, frac=20, nsample
     and the loss of both routes against the FP64 direct sum at nsample
     frequencies of q 0 (the route's discretisation in energy, second order in
     the step)."""
-    from paper_2603_12326_gb300 import QCX_FP64
+    import torch
+    from paper_2603_12326_gb300 import QCX_FP64, QCX_MIXED
     nw, ng = len(w), prob.ng
     step = eta / frac
     grids = [ctx.spectral_grid(iq, step) for iq in range(nq_spec)]
@@ -604,6 +608,46 @@ def spectral_leg(ctx, prob, G, w, eta, stream, fma, nq_spec=10, frac=20, nsample
                                         f"over the sampled w"}}
 
 
+def optical_leg(stream):
+    """The optical limit q -> 0 on the mid workload's cell, basis, k grid and G set
+    (a single q = 0 with conduction states at k, orthonormal together with the
+    valence states): for the three Cartesian directions, the pair densities with
+    the G = 0 row from the momentum matrix elements, chi0 over 200 w, inverse and
+    losses on the mixed path, timed with CUDA events; the head's loss peak."""
+    import torch
+
+    import synth
+    from paper_2603_12326_gb300 import QCX_MIXED, qcx, states
+
+    ctx = qcx.Context(torch.cuda.current_device(), stream=stream.cuda_stream)
+    p = synth.make_optical("mid")
+    states.load_optical(ctx, p)
+    G, w = p.G_int, p.w
+    g0 = int(np.flatnonzero(np.all(G == 0, axis=1))[0])
+    ctx.pair_density_optical(0, G, [1.0, 0.0, 0.0], QCX_MIXED)       # warm-up (momentum matrix, buffers)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    heads = {}
+    e0.record(stream)
+    for name, d in (("x", [1.0, 0.0, 0.0]), ("y", [0.0, 1.0, 0.0]), ("z", [0.0, 0.0, 1.0])):
+        ctx.pair_density_optical(0, G, d, QCX_MIXED)
+        ctx.chi0(0, w, p.eta, QCX_MIXED)
+        ctx.invert_eps(0, QCX_MIXED, want=False)
+        L1, L2 = ctx.loss_function(0, QCX_MIXED)
+        heads[name] = (L1[:, g0], L2[:, g0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    wev = w * 27.211386245988
+    out = {"workload": "mid workload's cell, basis, 8x8x8 k, N_v=4, N_c=32, N_G=181, q -> 0 along x, y, z, 200 w",
+           "value": 3 * len(w) / (ms / 1e3), "unit": "blocks/s", "ms_per_direction": ms / 3}
+    for name, (a, b) in heads.items():
+        out[f"head_{name}"] = {"L_lfe_peak_eV": float(wev[int(np.argmax(a))]), "L_lfe_max": float(np.max(a)),
+                               "L_nolfe_peak_eV": float(wev[int(np.argmax(b))]), "L_nolfe_max": float(np.max(b))}
+    return out
+
+
 def accuracy_sweep(ctx, prob, G, w, eta, outL, nsample=8):
     """Worst relative error of the mixed loss tables (outL[q][0|1][w][G], all
     200 w) against the FP64 GPU path at nsample frequencies of every q, per
@@ -671,7 +715,8 @@ def large_leg(stream, nq=2, nk_oracle=8):
     Lb, cnt = ctx.bin_loss(list(range(nq)), 0, edges, nw)
     nz = cnt > 0
     dR, dQ = ctx.rate(0.5 * (edges[1:] + edges[:-1])[nz], w, Lb[nz], halo, nQ=10)
-    L1, _ = ctx.loss_function(0, QCX_MIXED)
+    L1, L2 = ctx.loss_function(0, QCX_MIXED)
+    spec = _large_spectral(ctx, p, G, w, nq, stream, L1, L2)
     ctx.close()
     # the oracle on a bounded sample of the same workload
     from oracle import rpa
@@ -699,10 +744,50 @@ def large_leg(stream, nq=2, nk_oracle=8):
             "recoil_spectrum_note": f"FP64 rate over the |q+G| bins of the {nq} timed q (heavy mediator, "
                                     f"m_chi = 1 GeV)",
             "loss_table_finite": bool(np.all(np.isfinite(L1))),
+            "spectral": spec,
             "cpu_baseline": {"value": 1.0 / per_block, "unit": "blocks/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": f"1 q: pair densities for {nk_oracle}/{p.nk} k and chi0+eps+inverse+loss for "
                                        f"4/{nw} w over those transitions, scaled linearly in k",
                              "seconds": round(t2 - t0, 2)}}
+
+
+def _large_spectral(ctx, p, G, w, nq, stream, L1, L2, frac=40):
+    """The spectral route on the same q of the large workload (grid step eta/frac):
+    blocks/s over the per-q path with chi0 from the spectral function, the FP32
+    contraction's rate, and the loss of q 0 against the direct route's (L1, L2)
+    over all frequencies."""
+    import torch
+    from paper_2603_12326_gb300 import QCX_MIXED
+    nw, ng = len(w), p.ng
+    step = p.eta / frac
+    grids = [ctx.spectral_grid(iq, step) for iq in range(nq)]
+    ctx.pair_density(0, G, QCX_MIXED)                      # warm-up (buffers)
+    ctx.chi0_spectral(0, w, p.eta, grids[0][0], step, grids[0][1], QCX_MIXED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kk, wt, flops = 0.0, 0.0, 0.0
+    e0.record(stream)
+    for iq in range(nq):
+        E0, nbin = grids[iq]
+        ctx.pair_density(iq, G, QCX_MIXED)
+        ctx.chi0_spectral(iq, w, p.eta, E0, step, nbin, QCX_MIXED)
+        tm = ctx.spectral_timings()
+        kk += tm["contraction"]
+        wt += tm["weights"]
+        flops += 4.0 * nw * nbin * ng * (ng + 1)
+        ctx.invert_eps(iq, QCX_MIXED, want=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    S1, S2 = ctx.loss_function(0, QCX_MIXED)
+    return {"grid": f"step eta/{frac}, {grids[0][1]} points at q 0", "value": nq * nw / (ms / 1e3),
+            "unit": "blocks/s", "ms_per_q": ms / nq,
+            "contraction": {"kernel": "k_spec_kk<float>", "ms_per_q": kk / nq,
+                            "achieved_tflops": flops / (kk / 1e3) / 1e12},
+            "weights_ms_per_q": wt / nq,
+            "vs_direct_route": {"L_lfe": _masked_err(S1, L1), "L_nolfe": _masked_err(S2, L2),
+                                "sample": "q 0, all 400 w, every G; per spectrum where L > 1e-3 of its maximum; "
+                                          "both routes mixed"}}
 
 
 def batched_leg(stream, reps=10):
@@ -867,6 +952,29 @@ def run_profile_case(nw=50):
     print("profile case done")
 
 
+def run_profile_case_spectral(frac=20):
+    """q 0 of the mid workload through the mixed spectral route (grid step eta/frac,
+    all 200 w), twice: the launch configuration of the bench's spectral leg."""
+    import torch
+
+    import synth
+    from paper_2603_12326_gb300 import QCX_MIXED, qcx, states
+    from paper_2603_12326_gb300.build import build
+    build()
+    ctx = qcx.Context(0)
+    prob = synth.make_mid(nq=1)
+    states.load_problem(ctx, prob)
+    step = prob.eta / frac
+    E0, nbin = ctx.spectral_grid(0, step)
+    for _ in range(2):
+        ctx.pair_density(0, prob.G_int, QCX_MIXED)
+        ctx.chi0_spectral(0, prob.w, prob.eta, E0, step, nbin, QCX_MIXED)
+    ctx.sync()
+    torch.cuda.synchronize()
+    ctx.close()
+    print("profile case done")
+
+
 def _relaunch(n):
     """Re-run this command as n ranks (torch.distributed.run, 127.0.0.1)."""
     import socket
@@ -889,7 +997,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the accuracy sweep over every q")
     ap.add_argument("--no-large", action="store_true", help="skip the large-workload leg")
     ap.add_argument("--no-spectral", action="store_true", help="skip the spectral-route leg")
-    ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "mid200", "batch", "mlp"],
+    ap.add_argument("--profile-case", nargs="?", const="mid", choices=["mid", "mid200", "batch", "mlp", "spectral"],
                     help="small case for profilers, no report: mid = 1 q x 50 w of the mid workload, 2 passes; "
                          "batch = the uneven workload once; mlp = one gradient and one prediction")
     args = ap.parse_args()
@@ -914,6 +1022,8 @@ def main():
         run_profile_case_batch()
     elif args.profile_case == "mlp":
         run_profile_case_mlp()
+    elif args.profile_case == "spectral":
+        run_profile_case_spectral()
     elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:

@@ -160,6 +160,28 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
 qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_precision prec,
                             qcx_c64* out_rho);
 
+/* Pair densities in the optical limit q -> 0 along the direction qhat[3]
+ * (Appendix C, Eq. (ol_overlap) and the head and wing formulas after it), for a
+ * q number iq that is exactly zero and whose conduction states are at k itself
+ * (orthonormal together with the valence states, as eigenvectors of one H(k)).
+ * The G != 0 rows are the pair densities of qcx_pair_density at q = 0; the
+ * G = 0 row holds the limit of rho_t(0)/|q|,
+ *   rho~_t = -i qhat.p_t / dE_t,  p_t = <c k|grad|v k> (m_e = 1),
+ * from the momentum matrix of the Bloch sums (closed-form Gaussian gradient
+ * integrals, lattice sum kept as for the pair densities), and v^1/2 of that row
+ * is sqrt(4 pi) (the |q| factors cancel).  qcx_chi0 / qcx_chi0_spectral,
+ * qcx_invert_eps and qcx_loss_function then give the optical-limit matrix
+ * (head, wings, body) and its losses; the G = 0 entry of the loss tables is the
+ * optical loss along qhat (|q+G| = 0 there).  The momentum matrix is kept in
+ * the context while basis and states are unchanged.  qhat need not be
+ * normalised.  out_rho as in qcx_pair_density.
+ * Errors: QCX_ERR_STATE (no states), QCX_ERR_ARG (q number iq not zero, G = 0
+ * not in the list exactly once, qhat zero or non-finite, a transition with
+ * dE = 0, the arguments of qcx_pair_density), QCX_ERR_UNSUPPORTED (3 n_b n_v
+ * complex values above 227 KB of shared memory), QCX_ERR_ALLOC, QCX_ERR_CUDA. */
+qcx_status qcx_pair_density_optical(qcx_ctx* ctx, int iq, int ng, const int* G_int, const double* qhat,
+                                    qcx_precision prec, qcx_c64* out_rho);
+
 /* chi0_GG'(q,w) for nw frequencies w[nw] (Hartree) and broadening eta > 0
  * (Eq. (RPA)), followed in the same kernel by the Dyson step
  * eps = 1 - v^1/2 chi0 v^1/2, kept in the context.  Needs

@@ -324,6 +324,65 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
     return QCX_OK;
 }
 
+qcx_status qcx_pair_density_optical(qcx_ctx* ctx, int iq, int ng, const int* G_int, const double* qhat,
+                                    qcx_precision prec, qcx_c64* out_rho) {
+    if (!ctx) return QCX_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->nq) return ctx->fail(QCX_ERR_STATE, "pair_density_optical: no states");
+    if (iq < 0 || iq >= ctx->nq || ng < 1 || ng > 4096 || !G_int || !qhat ||
+        (prec != QCX_FP64 && prec != QCX_MIXED))
+        return ctx->fail(QCX_ERR_ARG, "pair_density_optical: bad arguments");
+    const double* q = &ctx->qpts[3 * iq];
+    if (q[0] != 0.0 || q[1] != 0.0 || q[2] != 0.0)
+        return ctx->fail(QCX_ERR_ARG, "pair_density_optical: q number iq must be zero");
+    cudaSetDevice(ctx->device);
+    std::vector<double> qh;
+    CUDA_OR_FAIL(fetch(ctx, qh, qhat, 3), "optical direction");
+    const double qn = std::sqrt(qh[0] * qh[0] + qh[1] * qh[1] + qh[2] * qh[2]);
+    if (!(qn > 0.0) || !std::isfinite(qn)) return ctx->fail(QCX_ERR_ARG, "pair_density_optical: bad direction");
+    const double dir[3] = {qh[0] / qn, qh[1] / qn, qh[2] / qn};
+    std::vector<int> Gh;
+    CUDA_OR_FAIL(fetch(ctx, Gh, G_int, 3 * (size_t)ng), "G list");
+    int g0 = -1, n0 = 0;
+    for (int g = 0; g < ng; ++g)
+        if (Gh[3 * g] == 0 && Gh[3 * g + 1] == 0 && Gh[3 * g + 2] == 0) {
+            g0 = g;
+            ++n0;
+        }
+    if (n0 != 1) return ctx->fail(QCX_ERR_ARG, "pair_density_optical: the G list must hold G = 0 exactly once");
+    qcx_status st = qcx_pair_density(ctx, iq, ng, G_int, prec, nullptr);
+    if (st != QCX_OK) return st;
+    QSlot& s = ctx->slot[prec];
+    s.have_rho = false;                                 // until the G = 0 row is in place
+    OpticalBufs& ob = ctx->optical;
+    CUDA_OR_FAIL(ob.status.ensure(sizeof(int)), "alloc");
+    CUDA_OR_FAIL(cudaMemsetAsync(ob.status.p, 0, sizeof(int), ctx->stream), "clear");
+    cudaError_t e = qcx_launch_optical(ctx, s, iq, g0, dir, prec, ob.status.as<int>());
+    if (e == cudaErrorInvalidValue)
+        return ctx->fail(QCX_ERR_UNSUPPORTED, "pair_density_optical: basis x valence bands too large for shared memory");
+    CUDA_OR_FAIL(e, "optical-limit kernels");
+    int bad = 0;
+    CUDA_OR_FAIL(cudaMemcpyAsync(&bad, ob.status.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status");
+    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream), "sync");
+    if (bad) return ctx->fail(QCX_ERR_ARG, "pair_density_optical: a transition with zero energy");
+    if (out_rho) {
+        const long long nt = (long long)ctx->nk * ctx->nv * ctx->nc;
+        const size_t nout = (size_t)nt * ng * sizeof(double2);
+        double2* dst = qcx_is_device_ptr(out_rho) ? reinterpret_cast<double2*>(out_rho) : nullptr;
+        if (!dst) {
+            CUDA_OR_FAIL(ctx->scratch.ensure(nout), "alloc");
+            dst = ctx->scratch.as<double2>();
+        }
+        k_rho_export<<<nblocks((size_t)nt * ng), 256, 0, ctx->stream>>>(
+            ng, nt, prec == QCX_FP64 ? s.rho.as<double2>() : nullptr,
+            reinterpret_cast<const __nv_bfloat162*>(s.rho.p), (long long)s.ngp * (s.kp / 2), s.kp / 2, dst);
+        CUDA_OR_FAIL(cudaGetLastError(), "export rho");
+        if (dst != reinterpret_cast<double2*>(out_rho)) CUDA_OR_FAIL(qcx_copy_out(ctx, out_rho, dst, nout), "copy out");
+    }
+    s.have_rho = true;
+    return QCX_OK;
+}
+
 qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, qcx_precision prec,
                     qcx_c64* out_chi0) {
     if (!ctx) return QCX_ERR_ARG;

@@ -108,6 +108,17 @@ struct BatchInst {
 struct BatchPlan;
 void qcx_batch_destroy(BatchPlan* p);
 
+// Optical limit: momentum matrix of the basis on the k grid (kept while basis and states are
+// unchanged) and the momentum elements of the current call.
+struct OpticalBufs {
+    DevBuf pairs;              // shell pairs with their lattice boxes
+    DevBuf P;                  // [nk][3][nb][nb] double2
+    DevBuf p;                  // [nt][3] double2 <c k|grad|v k>
+    DevBuf status;
+    unsigned long long gen = ~0ull;
+    int nk = 0;
+};
+
 // Work space of the spectral route to chi0 (one q at a time, either precision).
 struct SpecBufs {
     DevBuf bin, x;             // [nt] grid point and hat weight of each transition
@@ -187,6 +198,7 @@ struct qcx_ctx {
     int withhold_copies = 0;       // fault injection (tests): the per-q tensor-core kernel issues no copies
     MlpState* mlp = nullptr;       // surrogate network (parameters, Adam moments, work buffers)
     SpecBufs spec;                 // spectral route work space
+    OpticalBufs optical;           // optical-limit work space
     int spec_chunk_bins = 0;       // grid points per chunk of the spectral route (0: from a 4 GiB budget)
 
     ~qcx_ctx();
@@ -235,6 +247,11 @@ cudaError_t qcx_launch_qsetup(qcx_ctx* ctx, QSlot& s, const int* d_G, int ng, co
 cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precision prec);
 cudaError_t qcx_launch_overlap(qcx_ctx* ctx, int nk, const double* d_kpts, double2* d_out);
 cudaError_t qcx_pair_density_configure();
+
+// optical limit (optical.cu): momentum elements and the G = 0 row rho~ = -i qhat.p/dE of the
+// slot's pair densities, v^1/2 of that row set to sqrt(4 pi); d_status bit 1: a zero dE
+cudaError_t qcx_launch_optical(qcx_ctx* ctx, QSlot& s, int iq, int g0, const double qhat[3], qcx_precision prec,
+                               int* d_status);
 
 // chi0 (chi0_fp64.cu, chi0_tc.cu)
 cudaError_t qcx_launch_chi0_fp64(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out);

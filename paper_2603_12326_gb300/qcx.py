@@ -74,6 +74,7 @@ _SIGS = {
     "qcx_set_states": (I, [P, I, P, I, P, P, I, P, I, P, P]),
     "qcx_pair_density": (I, [P, I, I, P, I, P]),
     "qcx_chi0": (I, [P, I, I, P, D, I, P]),
+    "qcx_pair_density_optical": (I, [P, I, I, P, P, I, P]),
     "qcx_chi0_spectral": (I, [P, I, I, P, D, D, D, I, I, P, P]),
     "qcx_spectral_grid": (I, [P, I, D, ct.POINTER(D), ct.POINTER(I)]),
     "qcx_set_spectral_chunk": (I, [P, I]),
@@ -246,6 +247,17 @@ class Context:
         o = _out((self.nk * self.nv * self.nc, ng), np.complex128, out) if (want or out is not None) else None
         oa = _Arg(o, np.complex128)
         self._check(qcx_pair_density(self.h, iq, ng, g.ptr, prec, oa.ptr))
+        return o
+
+    def pair_density_optical(self, iq, G_int, qhat, prec=QCX_FP64, want=False, out=None):
+        """qcx_pair_density_optical: q number iq must be zero; G = 0 row = the q -> 0 limit along qhat."""
+        g = _Arg(G_int, np.int32)
+        qa = _Arg(np.asarray(qhat, np.float64), np.float64)
+        ng = len(G_int)
+        self._ng[prec] = ng
+        o = _out((self.nk * self.nv * self.nc, ng), np.complex128, out) if (want or out is not None) else None
+        oa = _Arg(o, np.complex128)
+        self._check(qcx_pair_density_optical(self.h, iq, ng, g.ptr, qa.ptr, prec, oa.ptr))
         return o
 
     def chi0(self, iq, w, eta, prec=QCX_FP64, want=False, out=None):
