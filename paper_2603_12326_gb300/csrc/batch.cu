@@ -239,7 +239,9 @@ std::vector<GEntry> g_union(const double* A, const double* q, double gmax) {
     return out;
 }
 
-// tensor-core tiles for a tile-width cap, grouped by slot group, largest N first
+// tensor-core tiles for a tile-width cap, grouped by slot group, largest N first and, within one
+// width, by q (slot), so the tiles that stream the same pair-density planes run side by side and
+// find them in L2
 void make_tc_tiles(const BatchPlan& p, int cap, std::vector<int4>& tiles, std::vector<int>& g0, std::vector<int>& gn) {
     const int ngrp = (p.nslot + QCX_BATCH_MAXQ - 1) / QCX_BATCH_MAXQ;
     std::vector<std::vector<int4>> grp(ngrp);
@@ -260,7 +262,11 @@ void make_tc_tiles(const BatchPlan& p, int cap, std::vector<int4>& tiles, std::v
     g0.clear();
     gn.clear();
     for (auto& v : grp) {
-        std::stable_sort(v.begin(), v.end(), [](const int4& x, const int4& y) { return (x.w & 0xFFFF) > (y.w & 0xFFFF); });
+        std::stable_sort(v.begin(), v.end(), [&](const int4& x, const int4& y) {
+            const int nx = x.w & 0xFFFF, ny = y.w & 0xFFFF;
+            if (nx != ny) return nx > ny;
+            return p.hinst[x.x].slot < p.hinst[y.x].slot;
+        });
         g0.push_back((int)tiles.size());
         gn.push_back((int)v.size());
         tiles.insert(tiles.end(), v.begin(), v.end());
