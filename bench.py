@@ -387,10 +387,10 @@ def run_ours(args, ws, rank, local):
                "seconds": round(secs, 2)}
 
     if rank == 0:
-        # per q: G setup, pair densities, W table, chi0, Gauss-Jordan, FP64 diagonal correction, loss by the
-        # quadratic form, |q+G|, the dielectric values kept for 3-D binning; per step two binnings and two rate +
-        # recoil pairs
-        launches_per_step = nq * 9 + 2 + 4
+        # per q: G setup, pair densities, W table, chi0, chi0 diagonal without cancellation, Gauss-Jordan, FP64
+        # diagonal correction, loss by the quadratic form, |q+G|, the dielectric values kept for 3-D binning; per
+        # step two binnings and two rate + recoil pairs
+        launches_per_step = nq * 10 + 2 + 4
         out = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "bf16",
@@ -557,11 +557,16 @@ def spectral_leg(ctx, prob, G, w, eta, stream, fma, nq_spec=10, frac=20, nsample
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    # q 0 again for its tables (the loop ended on the last q)
+    # q 0 again for its tables (the loop ended on the last q); then the same contraction on the
+    # CUDA cores in FP32 for comparison
     ctx.pair_density(0, G, QCX_MIXED)
     ctx.chi0_spectral(0, w, eta, grids[0][0], step, grids[0][1], QCX_MIXED)
     ctx.invert_eps(0, QCX_MIXED, want=False)
     Lm = ctx.loss_function(0, QCX_MIXED)
+    ctx.set_spectral_engine(True)
+    ctx.chi0_spectral(0, w, eta, grids[0][0], step, grids[0][1], QCX_MIXED)
+    cc_ms = ctx.spectral_timings()["contraction"]
+    ctx.set_spectral_engine(False)
     # FP64 route, q 0
     ctx.pair_density(0, G, QCX_FP64)
     torch.cuda.synchronize()
@@ -587,14 +592,21 @@ def spectral_leg(ctx, prob, G, w, eta, stream, fma, nq_spec=10, frac=20, nsample
                         f"({grids[0][1]} points at q 0)",
             "value": nq_spec * nw / (ms / 1e3), "unit": "blocks/s",
             "ms_per_q": ms / nq_spec,
-            "precision": "FP32 pair densities, weights and contraction (two-level sums, chunks added in FP64); "
-                         "grid and K in FP64; inverse as the mixed direct path",
-            "contraction": {"kernel": "k_spec_kk<float>", "bound": "alu", "ms_per_q": kk / nq_spec,
+            "precision": "FP32 pair densities and weights; contraction on tcgen05 in three-term split BF16 "
+                         "(FP32 sums restarted every 24 MMAs, chunks added in FP64); grid and K in FP64; inverse as "
+                         "the mixed direct path",
+            "contraction": {"kernel": "k_spec_kk_tc (with the K-major split of the weights, k_spec_s_split)",
+                            "bound": "tensor", "ms_per_q": kk / nq_spec,
                             "weights_ms_per_q": float(np.sum(wt_ms)) / nq_spec,
                             "flops": "4 FMA per (w, grid point, G <= G') pair",
-                            "achieved_tflops": achieved, "peak_tflops": fma.get("fp32_tflops"),
-                            "frac": achieved / fma["fp32_tflops"] if fma.get("fp32_tflops") else None,
-                            "peak_source": "FFMA microbenchmark measured in this run (libqcx_peaks)"},
+                            "achieved_tflops": achieved,
+                            "peak_tflops": _peaks().get("bf16_tflops_sustained"),
+                            "frac": achieved / _peaks().get("bf16_tflops_sustained", 1700.0),
+                            "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)",
+                            "cuda_cores_fp32": {"kernel": "k_spec_kk<float>", "ms_q0": cc_ms,
+                                                "achieved_tflops": 4.0 * nw * grids[0][1] * ng * (ng + 1) / (cc_ms / 1e3)
+                                                / 1e12,
+                                                "fp32_peak_tflops": fma.get("fp32_tflops")}},
             "fp64": {"value": nw / (ms64 / 1e3), "unit": "blocks/s", "sample": "q 0 (chi0 + inverse; pair "
                      "densities excluded)", "contraction_ms": tm64["contraction"], "weights_ms": tm64["weights"],
                      "contraction_tflops": ach64,
@@ -789,7 +801,7 @@ def _large_spectral(ctx, p, G, w, nq, stream, L1, L2, frac=40):
     F1, F2 = ctx.loss_function(0, QCX_FP64)
     return {"grid": f"step eta/{frac}, {grids[0][1]} points at q 0", "value": nq * nw / (ms / 1e3),
             "unit": "blocks/s", "ms_per_q": ms / nq,
-            "contraction": {"kernel": "k_spec_kk<float>", "ms_per_q": kk / nq,
+            "contraction": {"kernel": "k_spec_kk_tc", "ms_per_q": kk / nq,
                             "achieved_tflops": flops / (kk / 1e3) / 1e12},
             "weights_ms_per_q": wt / nq,
             "vs_fp64_spectral_route": {"spectral_mixed_L_lfe": _masked_err(S1, F1),

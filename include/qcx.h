@@ -209,9 +209,10 @@ qcx_status qcx_chi0(qcx_ctx* ctx, int iq, int nw, const double* w, double eta, q
  * in energy, second order in step) and eps = 1 - v^1/2 chi0 v^1/2 kept in the
  * context like qcx_chi0, for qcx_invert_eps.  Needs qcx_pair_density(iq) in
  * the same precision.  QCX_FP64: FP64 throughout.  QCX_MIXED: FP32 pair
- * densities (the mixed path's), FP32 spectral weights, FP32 contraction summed
- * in two levels (partial sums over 64 grid points, chunks of at most 4096
- * points added in FP64); grid and K in FP64.
+ * densities (the mixed path's), FP32 spectral weights, and the contraction
+ * over the grid points on the tcgen05 tensor cores with K and the weights as
+ * three-term split BF16 (FP32 sums restarted every 24 MMAs, added in FP32 per
+ * chunk of at most 4096 points, chunks added in FP64); grid and K in FP64.
  *   out_chi0[nw][ng][ng]  optional, row G, column G' (complex double)
  *   out_S[nbin][ng][ng]   optional spectral weights (complex double); large
  * Memory: the weights are formed in chunks of grid points (about 4 GiB, or
@@ -236,6 +237,12 @@ qcx_status qcx_spectral_grid(qcx_ctx* ctx, int iq, double step, double* E0, int*
  * chunk's spectral weights.  Results do not depend on it beyond rounding
  * (chunks are added in FP64).  Errors: QCX_ERR_ARG (ctx NULL, bins < 0). */
 qcx_status qcx_set_spectral_chunk(qcx_ctx* ctx, int bins);
+
+/* Engine of the mixed route's contraction in qcx_chi0_spectral: 0 (default)
+ * the tcgen05 tensor cores, nonzero the CUDA cores in FP32 (partial sums over
+ * 64 grid points added into a second FP32 sum), kept for comparison.  Library
+ * plumbing.  Errors: QCX_ERR_ARG (ctx NULL). */
+qcx_status qcx_set_spectral_engine(qcx_ctx* ctx, int cuda_cores);
 
 /* Device times (ms, CUDA events on the context's stream) of the stages of the
  * last qcx_chi0_spectral call: ms[0] grouping of the transitions by grid

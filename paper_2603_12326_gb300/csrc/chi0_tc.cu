@@ -386,6 +386,93 @@ __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, co
     }
 }
 
+// The diagonal of the mixed chi0 again, without the cancellation of the tensor-core GEMM:
+// there Im chi0_GG is formed from products of size |Re W| |rho|^2 that cancel to
+// |Im W| |rho|^2, so the split's 2^-24 is amplified by |w - dE|/eta far from resonance.
+// Here chi0_GG(w) = pref sum_t W_t(w) |rho_t(G)|^2 with |rho|^2 formed first (FP32 rho as
+// the sum of its three BF16 terms), FP32 sums over 256 transitions added in FP64; eps_GG =
+// 1 - v(G) chi0_GG is rewritten (and the chi0 diagonal, if kept).  CTA: 32 w x 32 G, thread
+// 2 x 2; transitions staged 32 at a time.
+__global__ void __launch_bounds__(256) k_diag_chi(int nw, int ng, long long nt, const float2* W, long long wld,
+                                                  const __nv_bfloat162* p0, const __nv_bfloat162* p1,
+                                                  const __nv_bfloat162* p2, long long kp2, double pref,
+                                                  const double* vs, double2* eps, double2* chi) {
+    __shared__ float2 Ws[32][33];            // [t][w]
+    __shared__ float Rs[32][33];             // [t][G]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int G0 = blockIdx.x * 32, w0 = blockIdx.y * 32;
+    float2 acc[2][2];
+    double2 acc64[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            acc[i][j] = make_float2(0.f, 0.f);
+            acc64[i][j] = make_double2(0.0, 0.0);
+        }
+    int chunk = 0;
+    for (long long t0 = 0; t0 < nt; t0 += 32) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = threadIdx.x + 256 * r;
+            const int tt = i & 31, row = i >> 5;
+            const long long t = t0 + tt;
+            float2 wv = make_float2(0.f, 0.f);
+            float rv = 0.f;
+            if (t < nt) {
+                if (w0 + row < nw) wv = W[(long long)(w0 + row) * wld + t];
+                if (G0 + row < ng) {
+                    const long long o = (long long)(G0 + row) * kp2 + t;
+                    const float2 a0 = __bfloat1622float2(p0[o]), a1 = __bfloat1622float2(p1[o]),
+                                 a2 = __bfloat1622float2(p2[o]);
+                    const float re = (a0.x + a1.x) + a2.x, im = (a0.y + a1.y) + a2.y;
+                    rv = re * re + im * im;
+                }
+            }
+            Ws[tt][row] = wv;
+            Rs[tt][row] = rv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int tt = 0; tt < 32; ++tt) {
+            const float2 wa = Ws[tt][ty], wb = Ws[tt][ty + 16];
+            const float ra = Rs[tt][tx], rb = Rs[tt][tx + 16];
+            acc[0][0].x = fmaf(wa.x, ra, acc[0][0].x);
+            acc[0][0].y = fmaf(wa.y, ra, acc[0][0].y);
+            acc[0][1].x = fmaf(wa.x, rb, acc[0][1].x);
+            acc[0][1].y = fmaf(wa.y, rb, acc[0][1].y);
+            acc[1][0].x = fmaf(wb.x, ra, acc[1][0].x);
+            acc[1][0].y = fmaf(wb.y, ra, acc[1][0].y);
+            acc[1][1].x = fmaf(wb.x, rb, acc[1][1].x);
+            acc[1][1].y = fmaf(wb.y, rb, acc[1][1].y);
+        }
+        __syncthreads();
+        if (++chunk == 8 || t0 + 32 >= nt) {
+            chunk = 0;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    acc64[i][j].x += (double)acc[i][j].x;
+                    acc64[i][j].y += (double)acc[i][j].y;
+                    acc[i][j] = make_float2(0.f, 0.f);
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int w = w0 + ty + 16 * i, G = G0 + tx + 16 * j;
+            if (w >= nw || G >= ng) continue;
+            const double2 ch = make_double2(pref * acc64[i][j].x, pref * acc64[i][j].y);
+            const double vv = vs[G] * vs[G];
+            const size_t o = ((size_t)w * ng + G) * ng + G;
+            eps[o] = make_double2(1.0 - vv * ch.x, -vv * ch.y);
+            if (chi) chi[o] = ch;
+        }
+}
+
 }  // namespace
 
 typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -490,5 +577,12 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     e = cudaFuncSetAttribute((const void*)k_chi0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_chi0_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mb[0], mb[1], mb[2], ms[0], ms[1], ms[2], a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const __nv_bfloat162* q0 = reinterpret_cast<const __nv_bfloat162*>(s.rho.p);
+    const long long plane2 = (long long)s.ngp * (s.kp / 2);
+    k_diag_chi<<<dim3((ng + 31) / 32, (s.nw + 31) / 32), 256, 0, ctx->stream>>>(
+        s.nw, ng, nt, s.wtab.as<float2>(), s.kp / 2, q0, q0 + plane2, q0 + 2 * plane2, s.kp / 2, a.pref,
+        s.vs.as<double>(), s.eps.as<double2>(), chi);
     return cudaGetLastError();
 }

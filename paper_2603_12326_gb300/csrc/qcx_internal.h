@@ -131,6 +131,7 @@ struct SpecBufs {
     DevBuf S;                  // spectral weights of one chunk of grid points
     DevBuf chi;                // [nw][ng][ng] double2 chi0 accumulated over the chunks
     DevBuf Sout;               // staging of exported weights
+    DevBuf kplanes, splanes;   // mixed route on the tensor cores: K table and chunk weights as BF16 planes
     // stage times of the last call (CUDA events on the context's stream): grouping, gather and
     // K table, spectral weights, contraction, Dyson step (ms)
     std::vector<cudaEvent_t> ev;
@@ -200,6 +201,7 @@ struct qcx_ctx {
     SpecBufs spec;                 // spectral route work space
     OpticalBufs optical;           // optical-limit work space
     int spec_chunk_bins = 0;       // grid points per chunk of the spectral route (0: from a 4 GiB budget)
+    int spec_cuda_cores = 0;       // mixed spectral contraction on the CUDA cores (FP32) instead of tcgen05
 
     ~qcx_ctx();
     qcx_status fail(qcx_status s, const std::string& msg) {
@@ -252,6 +254,16 @@ cudaError_t qcx_pair_density_configure();
 // slot's pair densities, v^1/2 of that row set to sqrt(4 pi); d_status bit 1: a zero dE
 cudaError_t qcx_launch_optical(qcx_ctx* ctx, QSlot& s, int iq, int g0, const double qhat[3], qcx_precision prec,
                                int* d_status);
+
+// spectral route on the tensor cores (spectral_tc.cu): K table as three BF16 planes [rows][ld]
+// (row 2 w + r); one chunk's weights [pair][point][32][32] split into three K-major planes and
+// contracted with the K planes into chi (FP64, stored or added)
+cudaError_t qcx_spec_tc_ktab(cudaStream_t st, int nw, int rows, long long ld, int nbin, const double* w, double E0,
+                             double step, double eta, __nv_bfloat16* planes);
+cudaError_t qcx_spec_tc_contract(cudaStream_t st, const CUtensorMap* kmaps, const CUtensorMap* smaps, int mtiles,
+                                 int ntiles, int nw, int ng, int nbc, int nb, int kb0, long long sld, const float2* S,
+                                 __nv_bfloat16* splanes, const int2* tp, int accumulate, double2* chi, int* status,
+                                 long long wait_limit);
 
 // chi0 (chi0_fp64.cu, chi0_tc.cu)
 cudaError_t qcx_launch_chi0_fp64(qcx_ctx* ctx, QSlot& s, int iq, double2* d_chi0_out);

@@ -27,11 +27,13 @@
 //   k_spec_dyson    eps in the layout of the slot (FP64: [w][G][G'], MIXED: [w][G'][G]).
 //
 // Precision: FP64 throughout (QCX_FP64), or FP32 pair densities (the sum of the three
-// BF16 terms of the mixed path), FP32 spectral weights and an FP32 contraction summed in two
-// levels, partial sums over 64 grid points added into a second FP32 accumulator, over chunks
-// of at most 4096 grid points (QCX_MIXED); K and the grid are formed in FP64 in both.  The
-// grid points are processed in chunks whose spectral weights fit a memory budget; chi0 is
-// accumulated over the chunks in FP64.
+// BF16 terms of the mixed path), FP32 spectral weights and the contraction on the tcgen05
+// tensor cores in three-term split BF16 (spectral_tc.cu; QCX_MIXED); K and the grid are formed
+// in FP64 in both.  The grid points are processed in chunks whose spectral weights fit a
+// memory budget (at most 4096 points for the mixed route); chi0 is accumulated over the
+// chunks in FP64.  The mixed contraction can also run on the CUDA cores in FP32
+// (qcx_set_spectral_engine), summed in two levels: partial sums over 64 grid points added
+// into a second FP32 accumulator.
 #include "qcx_internal.h"
 #include "cplx.cuh"
 
@@ -259,12 +261,16 @@ template <typename R> __global__ void __launch_bounds__(256) k_spec_gram(GramArg
         }
         __syncthreads();
     }
+    // S_b is Hermitian: its diagonal is real, so the rounding left in the imaginary part there
+    // (which Re K would carry into Im chi0_GG) is dropped
     C* out = a.S + ((size_t)p * a.nbc + bl) * SP_TILE2;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
-            out[(ty + 16 * i) * SP_TILE + tx + 16 * j] = mk<R>(a.pref * acc[i][j].x, a.pref * acc[i][j].y);
+        for (int j = 0; j < 2; ++j) {
+            const bool diag = pr.x == pr.y && ty + 16 * i == tx + 16 * j;
+            out[(ty + 16 * i) * SP_TILE + tx + 16 * j] = mk<R>(a.pref * acc[i][j].x, diag ? (R)0 : a.pref * acc[i][j].y);
+        }
 }
 
 // full Hermitian S_b [b][G][G'] (FP64) from the upper tiles of one chunk
@@ -552,6 +558,26 @@ qcx_status spectral_chi0(qcx_ctx* ctx, QSlot& s, bool mixed, int nw, double E0, 
                  "contraction smem");
     const R pref = (R)(2.0 / (ctx->nk * cell_volume(ctx)));
     const int nchunk = (int)((nbin + nbc - 1) / nbc);
+    // the mixed route's contraction on the tensor cores: K table and each chunk's weights as
+    // three BF16 planes, K-major over the grid points
+    const bool tc = mixed && !ctx->spec_cuda_cores;
+    const int mtiles = (2 * nw + 127) / 128;
+    const int ntiles = ntp * 16;                      // 2 x 1024 columns per tile pair, 128 per tile
+    CUtensorMap kmaps[3], smaps[3];
+    if (tc) {
+        const size_t kn = (size_t)mtiles * 128 * ldk;
+        const size_t sn = (size_t)ntiles * 128 * nbc;
+        CUDA_OR_FAIL(sp.kplanes.ensure(3 * kn * sizeof(__nv_bfloat16)), "alloc K planes");
+        CUDA_OR_FAIL(sp.splanes.ensure(3 * sn * sizeof(__nv_bfloat16)), "alloc weight planes");
+        CUDA_OR_FAIL(qcx_spec_tc_ktab(st, nw, mtiles * 128, ldk, nbin, s.w.as<double>(), E0, step, s.eta,
+                                      sp.kplanes.as<__nv_bfloat16>()),
+                     "K planes kernel");
+        for (int i = 0; i < 3; ++i)
+            if (!qcx_make_bf16_map(&kmaps[i], sp.kplanes.as<__nv_bfloat16>() + i * kn, ldk, mtiles * 128, 128, 32) ||
+                !qcx_make_bf16_map(&smaps[i], sp.splanes.as<__nv_bfloat16>() + i * sn, nbc, ntiles * 128, 128, 32))
+                return ctx->fail(QCX_ERR_CUDA, "chi0_spectral: tensor map encoding failed");
+        CUDA_OR_FAIL(cudaMemsetAsync(sp.status.p, 0, sizeof(int), st), "clear");
+    }
     CUDA_OR_FAIL(sp.events(3 + 3 * (size_t)nchunk + 1), "events");
     CUDA_OR_FAIL(cudaEventRecord(sp.ev[2], st), "event");
 
@@ -583,6 +609,15 @@ qcx_status spectral_chi0(qcx_ctx* ctx, QSlot& s, bool mixed, int nw, double E0, 
                              "copy out weights");
         }
         CUDA_OR_FAIL(cudaEventRecord(ce[1], st), "event");
+        if (tc) {
+            CUDA_OR_FAIL(qcx_spec_tc_contract(st, kmaps, smaps, mtiles, ntiles, nw, ng, (int)nbc, nb, (int)b0, nbc,
+                                              reinterpret_cast<const float2*>(sp.S.p),
+                                              sp.splanes.as<__nv_bfloat16>(), sp.tp.as<int2>(), b0 > 0 ? 1 : 0,
+                                              sp.chi.as<double2>(), sp.status.as<int>(), ctx->wait_limit),
+                         "tensor-core contraction");
+            CUDA_OR_FAIL(cudaEventRecord(ce[2], st), "event");
+            continue;
+        }
         KKArgs<R> ka;
         ka.S = sp.S.as<C>();
         ka.K = sp.ktab.as<C>();
@@ -621,6 +656,12 @@ qcx_status spectral_chi0(qcx_ctx* ctx, QSlot& s, bool mixed, int nw, double E0, 
     CUDA_OR_FAIL(cudaEventElapsedTime(&t, sp.ev[3 + 3 * (size_t)(nchunk - 1) + 2], end), "timing");
     ms[4] = t;
     for (int i = 0; i < 5; ++i) sp.ms[i] = ms[i];
+    if (tc) {
+        int bad = 0;
+        CUDA_OR_FAIL(cudaMemcpyAsync(&bad, sp.status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+        CUDA_OR_FAIL(cudaStreamSynchronize(st), "sync");
+        if (bad) return ctx->fail(QCX_ERR_TIMEOUT, "chi0_spectral: a pipeline wait in the tensor-core kernel gave up");
+    }
     return QCX_OK;
 }
 
@@ -650,6 +691,13 @@ extern "C" qcx_status qcx_spectral_grid(qcx_ctx* ctx, int iq, double step, doubl
     if (!(nb <= (double)(INT_MAX / 2))) return ctx->fail(QCX_ERR_ARG, "spectral_grid: too many grid points");
     *E0 = e0;
     *nbin = (int)nb;
+    return QCX_OK;
+}
+
+extern "C" qcx_status qcx_set_spectral_engine(qcx_ctx* ctx, int cuda_cores) {
+    if (!ctx) return QCX_ERR_ARG;
+    ctx->err.clear();
+    ctx->spec_cuda_cores = cuda_cores ? 1 : 0;
     return QCX_OK;
 }
 

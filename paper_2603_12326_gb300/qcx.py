@@ -78,6 +78,7 @@ _SIGS = {
     "qcx_chi0_spectral": (I, [P, I, I, P, D, D, D, I, I, P, P]),
     "qcx_spectral_grid": (I, [P, I, D, ct.POINTER(D), ct.POINTER(I)]),
     "qcx_set_spectral_chunk": (I, [P, I]),
+    "qcx_set_spectral_engine": (I, [P, I]),
     "qcx_spectral_timings": (I, [P, P]),
     "qcx_invert_eps": (I, [P, I, I, P, P, P]),
     "qcx_set_refine_threshold": (I, [P, D]),
@@ -293,6 +294,9 @@ class Context:
 
     def set_spectral_chunk(self, bins):
         self._check(qcx_set_spectral_chunk(self.h, int(bins)))
+
+    def set_spectral_engine(self, cuda_cores: bool):
+        self._check(qcx_set_spectral_engine(self.h, 1 if cuda_cores else 0))
 
     def spectral_timings(self):
         """Stage times (ms) of the last chi0_spectral call: grouping, gather + K table,

@@ -274,6 +274,133 @@ def test_batch_kernel_protocol_across_tiles(kstages, ntile):
         assert not errors, (kstages, ntile, seed, errors[:3])
 
 
+def _run_spec(kstages, nstage, promote, seed, timeouts=False, withhold=False):
+    """One random schedule of k_spec_kk_tc: both operands come by TMA, so the
+    issuers wait on the copies themselves, and eight warps only drain the
+    windows in order."""
+    rnd = random.Random(seed)
+    nwarp = 8
+    nb = 2 * nstage
+    full = [_Bar(1) for _ in range(nb)]
+    empty = [_Bar(1) for _ in range(nstage)]
+    acc_full = [_Bar(1), _Bar(1)]
+    drained = [_Bar(nwarp), _Bar(nwarp)]
+    mma_done_bar = _Bar(2)
+    landed, mma_done, drain_done = set(), set(), {}
+    copies, mmas, errors, issued = [], [], [], []
+    state = {"abort": False}
+    nwin = (kstages + promote - 1) // promote
+
+    def wait(bar, parity, event_happened, what, honour_abort=True):
+        spins = 0
+        while not bar.passes(parity):
+            if honour_abort and state["abort"]:
+                return False
+            spins += 1
+            if honour_abort and timeouts and spins > 8 and rnd.random() < 0.01:
+                state["abort"] = True
+                return False
+            yield
+        if not event_happened():
+            errors.append("early pass: " + what)
+        return True
+
+    def producer():
+        for gs in range(0 if withhold else kstages):
+            s, ph = gs % nstage, (gs // nstage) & 1
+            ok = yield from wait(empty[s], ph ^ 1, lambda gs=gs: gs < nstage or (gs - nstage) in mma_done,
+                                 "stage %d free" % gs)
+            if not ok:
+                break
+            copies.append((gs, gs % nb))
+            issued.append(gs)
+        for gs in issued[-nstage:]:
+            yield from wait(full[gs % nb], (gs // nb) & 1, lambda gs=gs: gs in landed, "copy %d" % gs,
+                            honour_abort=False)
+        if copies:
+            errors.append("producer left with copies in flight")
+
+    def drainer():
+        for wd in range(nwin):
+            ok = yield from wait(acc_full[wd & 1], (wd >> 1) & 1, lambda wd=wd: ("win", wd) in mma_done,
+                                 "window %d" % wd)
+            if not ok:
+                return
+            drain_done[wd] = drain_done.get(wd, 0) + 1
+            drained[wd & 1].arrive()
+
+    def issuer(par):
+        ok = True
+        for wd in range(par, nwin, 2):
+            b = wd & 1
+            if wd >= 2:
+                ok = yield from wait(drained[b], ((wd - 2) >> 1) & 1, lambda w=wd: drain_done.get(w - 2, 0) == nwarp,
+                                     "buffer of window %d drained" % wd)
+                if not ok:
+                    break
+            for gs in range(wd * promote, min((wd + 1) * promote, kstages)):
+                ok = yield from wait(full[gs % nb], (gs // nb) & 1, lambda gs=gs: gs in landed, "copy %d" % gs)
+                if not ok:
+                    break
+                mmas.append((gs, [empty[gs % nstage]]))
+                yield
+            if not ok:
+                break
+            mmas.append((("win", wd), [acc_full[b]]))
+            yield
+        mmas.append((("done", par), [mma_done_bar]))
+        yield from wait(mma_done_bar, 0, lambda: ("done", 0) in mma_done and ("done", 1) in mma_done,
+                        "every MMA finished", honour_abort=False)
+
+    actors = [producer(), issuer(0), issuer(1)] + [drainer() for _ in range(nwarp)]
+    alive = [True] * len(actors)
+    for _ in range(2000000):
+        if not any(alive):
+            if mmas:
+                errors.append("TMEM freed with MMAs in flight")
+            if not state["abort"] and len(drain_done) != nwin:
+                errors.append("work missing without an abort")
+            if withhold and not state["abort"]:
+                errors.append("withheld copies did not abort the kernel")
+            return errors, state["abort"]
+        r = rnd.random()
+        if r < 0.15 and copies:
+            gs, s2 = copies.pop(rnd.randrange(len(copies)))
+            landed.add(gs)
+            full[s2].arrive()
+        elif r < 0.3 and mmas:
+            key, bars = mmas.pop(0)
+            mma_done.add(key)
+            for bar in bars:
+                bar.arrive()
+        else:
+            live = [i for i, a in enumerate(alive) if a]
+            i = rnd.choice(live)
+            try:
+                next(actors[i])
+            except StopIteration:
+                alive[i] = False
+    return errors + ["no progress (deadlock)"], None
+
+
+@pytest.mark.parametrize("kstages", [1, 2, 3, 5, 8, 13, 40, 128])
+def test_spectral_kernel_protocol(kstages):
+    """k_spec_kk_tc (the spectral route's contraction): ring depth, window and
+    barrier counts read from its source; random schedules with and without
+    waits that give up, and with the copies withheld."""
+    src = _src("spectral_tc.cu")
+    nstage, promote = _constant("SK_NSTAGE", "spectral_tc.cu"), _constant("SK_PROMOTE", "spectral_tc.cu")
+    assert "mbar_init(&drained[b], 8)" in src and src.count("% (2 * SK_NSTAGE)") >= 3
+    assert "for (int it = max(0, last - SK_NSTAGE + 1); it <= last; ++it)" in src
+    for seed in range(15):
+        errors, aborted = _run_spec(kstages, nstage, promote, seed)
+        assert not errors and not aborted, (kstages, seed, errors[:3])
+        errors, _ = _run_spec(kstages, nstage, promote, seed, timeouts=True)
+        assert not errors, (kstages, seed, errors[:3])
+        errors, aborted = _run_spec(kstages, nstage, promote, seed, timeouts=True, withhold=True)
+        assert not errors and aborted, (kstages, seed, errors[:3])
+
+
 def test_short_ring_is_caught():
     """A window longer than the ring (five stages per window on a ring of
     two) lets an issuer's wait on an A-tile barrier pass one phase early."""

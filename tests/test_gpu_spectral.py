@@ -75,15 +75,21 @@ def test_fp64_spectral_route_matches_oracle(small, chunk):
         assert np.max(np.abs(S[b] - S[b].conj().T)) <= 1e-13 * top
 
 
-def test_mixed_spectral_route_at_the_mixed_bar(small):
+@pytest.mark.parametrize("engine", ["tensor", "cuda_cores"])
+@pytest.mark.parametrize("chunk", [0, 64])
+def test_mixed_spectral_route_at_the_mixed_bar(small, engine, chunk):
+    """Both engines of the mixed contraction (tcgen05 split BF16, CUDA-core FP32),
+    in one chunk and in chunks of 64 grid points."""
     p, iq, Ck, Ckq, o = small
     ctx = _ctx(p, iq, Ck, Ckq, QCX_MIXED)
+    ctx.set_spectral_engine(engine == "cuda_cores")
+    ctx.set_spectral_chunk(chunk)
     chi, _ = ctx.chi0_spectral(0, p.w, p.eta, o["E0"], o["step"], o["nbin"], QCX_MIXED, want=True)
     ctx.invert_eps(0, QCX_MIXED, want=False)
     L1, L2 = ctx.loss_function(0, QCX_MIXED)
     ctx.close()
     e = rel(chi, o["chi"]), rel_spectrum(L1, o["L_lfe"]), rel_spectrum(L2, o["L_nolfe"])
-    print("mixed spectral route vs oracle: chi0 %.2e, L_LFE %.2e, L_noLFE %.2e" % e)
+    print(f"mixed spectral route ({engine}, chunk {chunk}) vs oracle: chi0 %.2e, L_LFE %.2e, L_noLFE %.2e" % e)
     assert e[0] < 5e-5 and e[1] < 1e-4 and e[2] < 1e-4
 
 
