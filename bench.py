@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one k_chi0_tc launch over 1 q x 200 w of the mid workload, from one ncu capture
 # of `bench.py --profile-case mid200` (dram__bytes_read.sum + dram__bytes_write.sum), and the commit of the kernel
 # source it was taken at; None once the kernel has changed since.
-CHI0_TRAFFIC = {"bytes": 923402240 + 182239232, "commit": "debafdc"}
+CHI0_TRAFFIC = None
 # Executed FP32 flops of one k_pair_density_fused launch over 1 q of the mid workload (512 k x 181 G), from the
 # ncu thread-instruction counters of `bench.py --profile-case mid` (2 FFMA + FADD + FMUL,
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), and the commit of the kernel source.
@@ -395,9 +395,10 @@ def run_ours(args, ws, rank, local):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "bf16",
                "data": "synthetic (seeded states shaped like the paper's workloads)",
-               "config": _config(ws, "chi0 as three-term split-BF16 products (the six of order <= 2) with FP32 "
-                                     "accumulation restarted every 24 MMAs and FP64 partial sums; pair densities "
-                                     "FP32; inverse FP32 + FP64 diagonal correction; rate FP64", nq * nw),
+               "config": _config(ws, "chi0 as split-BF16 tcgen05 products: rho~ (two BF16 terms of the FP32 "
+                                     "pair densities) against W rho~ in three terms, five products, FP32 "
+                                     "accumulation restarted every 20 MMAs and FP64 partial sums, diagonal summed "
+                                     "again in FP32; inverse FP32 + FP64 diagonal correction; rate FP64", nq * nw),
                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak,
                             "traffic": CHI0_TRAFFIC["bytes"] if CHI0_TRAFFIC else None,

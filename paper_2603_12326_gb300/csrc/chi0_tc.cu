@@ -5,17 +5,26 @@
 // is one real GEMM per q,
 //   D[m][n] = sum_k A[m][k] B[n][k],   k = 2t + p (p = 0 real, 1 imaginary part),
 //   n = G,  m = (G'-block, w, re|im, G' in block),
-//   B[G][2t+p]           = (Re, Im) rho_t(G)                                 (operand read by TMA)
-//   A[(w,re,G')][2t+p]   = (Re, Im) (W_t(w) rho_t(G'))                      (generated in shared memory)
-//   A[(w,im,G')][2t+p]   = (Im, -Re)(W_t(w) rho_t(G')),
-// so the re rows of D hold Re chi0_GG' and the im rows Im chi0_GG'.  Both
-// operands are split into three BF16 terms x = x0 + x1 + x2 (x0 = bf16(x),
-// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)); D accumulates in FP32 the six
-// products whose order is at most 2, a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0,
-// so each product carries ~2^-24 relative error (the two-term split's 2^-16
-// is too coarse once the inverse amplifies it by the condition number of eps).
-// W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is tabulated per q by
-// k_weights with dE and w -+ dE in FP64 and fetched with each K stage.
+//   B[G][2t+p]           = (Re, Im) rho~_t(G)                                (operand read by TMA)
+//   A[(w,re,G')][2t+p]   = (Re, Im) (W_t(w) rho~_t(G'))                     (generated in shared memory)
+//   A[(w,im,G')][2t+p]   = (Im, -Re)(W_t(w) rho~_t(G')),
+// so the re rows of D hold Re chi0_GG' and the im rows Im chi0_GG'.
+//
+// Precision.  B is rho~ = b0 + b1, the first two BF16 terms of the FP32 pair
+// densities (16 significant bits), held exactly by the two planes; A is built
+// from the same rho~ and split into three BF16 terms a = a0 + a1 + a2 (24 bits);
+// D accumulates in FP32 the five products a0 b0 + a0 b1 + a1 b0 + a1 b1 + a2 b0
+// (the one left out, a2 b1, is ~2^-24 of a b).  Because both sides carry the
+// same rho~, the truncation of B is not an error of the contraction: the result
+// is chi0 of the pair densities rho~ (a relative change of 2^-17 in each, which
+// keeps the Hermitian part from Re W and the anti-Hermitian part from Im W
+// apart).  Only the A side's 2^-24 and the dropped product are errors of the
+// contraction, and those are what the inverse's condition number and the
+// cancellation |Re W| |rho|^2 -> |Im W| |rho|^2 amplify.  (Truncating both sides to
+// two terms with three or four products leaves 2^-17 on A and misses 1e-4 on
+// the loss with local fields; two FP16 terms, scaled by powers of two, missed
+// it too.)  W_t(w) = 1/(w - dE + i eta) - 1/(w + dE + i eta) is tabulated per q
+// by k_weights with dE and w -+ dE in FP64 and fetched with each K stage.
 //
 // The tensor core's FP32 accumulation truncates, so long sums drift (about
 // 2^-24 of the running value per MMA, always toward zero).  The accumulator
@@ -23,20 +32,17 @@
 // in turn, the finished buffer is drained into FP32 registers (round to
 // nearest), and every FLUSH stages the register partials are added into an
 // FP64 buffer owned by the CTA.  The Dyson step runs in FP64 from that
-// buffer and eps is stored in FP64.  (Two BF16 terms with three or four
-// products leave 2^-17 of every operand and miss 1e-4 on the loss with local
-// fields at some q; two FP16 terms, scaled by powers of two, missed it too,
-// although a host emulation that keeps FP16 subnormals meets it.)
+// buffer and eps is stored in FP64.
 //
 // CTA work item: one 64-row G' block, one frequency (a 128 x N accumulator:
-// 64 re rows and 64 im rows), one N chunk of G.  Warp roles: warp 0 issues
-// TMA loads of the B tiles (and, when the G range is split, of the A-source
-// rows); warp 1 owns TMEM; one thread of warp 1 issues the MMAs of the even
-// accumulation windows and one thread of warp 10 those of the odd windows;
-// warps 2-9 form W and the A tiles, drain the accumulators and run the
-// epilogue (eps = delta - v^1/2 chi0 v^1/2); warp 11 idles.  Every wait is bounded: on timeout the
-// kernel records an error status, lets its own copies and MMAs finish, frees
-// TMEM and returns.
+// 64 re rows and 64 im rows), one N chunk of G.  Warp roles (five warpgroups):
+// warp 0 issues TMA loads of the B tiles (and, when the G range is split, of the
+// A-source rows); warp 1 owns TMEM; one thread of warp 1 issues the MMAs of the
+// even accumulation windows and one thread of warp 2 those of the odd windows;
+// warps 4-11 form W and the A tiles; warps 12-19 drain the accumulators and run
+// the epilogue (eps = delta - v^1/2 chi0 v^1/2).  Every wait is bounded: on
+// timeout the kernel records an error status, lets its own copies and MMAs
+// finish, frees TMEM and returns.
 #include "qcx_internal.h"
 #include "tc_ptx.cuh"
 
@@ -44,10 +50,24 @@
 
 namespace {
 
-constexpr int NTHREADS = 384;                // warps: 0 TMA, 1 and 10 MMA, 2-9 A/drain/epilogue, 11 idle
-constexpr int MMA_WARP2 = 10;
-constexpr int NSTAGE = 3;
-constexpr int NPIECE = 3;                 // BF16 terms per operand
+// Five warpgroups.  WG0: warp 0 issues the TMA copies, warp 1 owns TMEM and with warp 2 issues
+// the MMAs (alternate accumulation windows), warp 3 idles.  WG1-WG2 (warps 4-11) form W rho~
+// and the A tiles.  WG3-WG4 (warps 12-19) drain the accumulators and run the epilogue.  A
+// generation and the drain run in separate warps so that neither waits for the other; the
+// drain warps hold 96 FP32 partial sums each, so the warpgroups trade registers (setmaxnreg):
+// 40 for WG0, 64 for the A warps, 152 for the drain warps, 60416 in all of the 640 x 96
+// the block is launched with (the launch is refused if the kernel was built with another count).
+constexpr int NTHREADS = 640;
+constexpr int LAUNCH_REGS = 96;              // 65536 / 640, rounded down to the allocation granule
+constexpr int REG_CTRL = 40, REG_AGEN = 64, REG_DRAIN = 152;
+static_assert(128 * REG_CTRL + 256 * REG_AGEN + 256 * REG_DRAIN <= NTHREADS * LAUNCH_REGS,
+              "warpgroup register budgets exceed the launch allocation");
+constexpr int MMA_WARP2 = 2;
+constexpr int AGEN_WARP0 = 4;                // first A-generation warp (8 warps)
+constexpr int DRAIN_WARP0 = 12;              // first drain/epilogue warp (8 warps)
+constexpr int NSTAGE = 4;
+constexpr int NPA = 3;                    // BF16 terms of the A operand (W rho~)
+constexpr int NPB = 2;                    // BF16 terms of the B operand (rho~ = b0 + b1)
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per half tile
 constexpr int PROMOTE = 2;                // K stages accumulated in one TMEM buffer
@@ -75,8 +95,7 @@ struct TcArgs {
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_chi0_tc(const __grid_constant__ CUtensorMap mb0, const __grid_constant__ CUtensorMap mb1,
-              const __grid_constant__ CUtensorMap mb2, const __grid_constant__ CUtensorMap ms0,
-              const __grid_constant__ CUtensorMap ms1, const __grid_constant__ CUtensorMap ms2, TcArgs a) {
+              const __grid_constant__ CUtensorMap ms0, const __grid_constant__ CUtensorMap ms1, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -84,9 +103,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int n0 = blockIdx.y * a.n_tile;
     const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;          // one B piece
     const uint32_t spiece = (uint32_t)GBLK * ROWB;              // one A-source piece
-    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * spiece;
-    const uint32_t aoff = NPIECE * bbytes + sbytes;             // A pieces start here in a stage
-    const uint32_t stage_bytes = aoff + NPIECE * ATILE;
+    const uint32_t sbytes = a.src_from_b ? 0u : NPB * spiece;
+    const uint32_t aoff = NPB * bbytes + sbytes;                // A pieces start here in a stage
+    const uint32_t stage_bytes = aoff + NPA * ATILE;
     constexpr int TPS = KSTEP / 2;                              // transitions per stage
     unsigned char* tail = base + NSTAGE * stage_bytes;
     float2* Wbuf = reinterpret_cast<float2*>(tail);             // [NSTAGE][TPS]
@@ -124,167 +143,116 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
 
-    if (warp == 0) {
-        // ---------------------------------------------------------- TMA producer
-        if (lane == 0) {
-            // a stage's lines are requested into L2 a few stages before its copy is issued
-            auto prefetch = [&](int it) {
-                bulk_prefetch(a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2));
-                tma_prefetch_2d(&mb0, it * KSTEP, n0);
-                tma_prefetch_2d(&mb1, it * KSTEP, n0);
-                tma_prefetch_2d(&mb2, it * KSTEP, n0);
-                if (!a.src_from_b) {
-                    tma_prefetch_2d(&ms0, it * KSTEP, gb * GBLK);
-                    tma_prefetch_2d(&ms1, it * KSTEP, gb * GBLK);
-                    tma_prefetch_2d(&ms2, it * KSTEP, gb * GBLK);
-                }
-            };
-            for (int it = 0; it < PREFETCH && it < a.kstages; ++it) prefetch(it);
-            int last = -1;
-            // with copies withheld (fault injection for tests) nothing is issued, so the
-            // consumers' first waits run out and the kernel reports a timeout
-            for (int it = 0; it < (a.withhold ? 0 : a.kstages); ++it) {
-                const int s = it % NSTAGE;
-                const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
-                if (it + PREFETCH < a.kstages) prefetch(it + PREFETCH);
-                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status, a.wait_limit)) break;
-                uint64_t* fb = &full_b[it % (2 * NSTAGE)];
-                unsigned char* st = base + s * stage_bytes;
-                mbar_arrive_tx(fb, NPIECE * bbytes + sbytes + TPS * (uint32_t)sizeof(float2));
-                bulk_load(Wbuf + s * TPS, a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2), fb);
-                tma_load_2d(st, &mb0, fb, it * KSTEP, n0);
-                tma_load_2d(st + bbytes, &mb1, fb, it * KSTEP, n0);
-                tma_load_2d(st + 2 * bbytes, &mb2, fb, it * KSTEP, n0);
-                if (!a.src_from_b) {
-                    unsigned char* sp = st + NPIECE * bbytes;
-                    tma_load_2d(sp, &ms0, fb, it * KSTEP, gb * GBLK);
-                    tma_load_2d(sp + spiece, &ms1, fb, it * KSTEP, gb * GBLK);
-                    tma_load_2d(sp + 2 * spiece, &ms2, fb, it * KSTEP, gb * GBLK);
-                }
-                last = it;
-            }
-            // let every copy still in flight (at most the last NSTAGE stages) land before the CTA can exit
-            for (int it = max(0, last - NSTAGE + 1); it <= last; ++it)
-                mbar_wait(&full_b[it % (2 * NSTAGE)], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag, a.status,
-                          CLEANUP_WAIT_LIMIT, false);
-        }
-    } else if (warp == 1 || warp == MMA_WARP2) {
-        // ---------------------------------------------------------- MMA issuers
-        // Issuing tcgen05.mma keeps the issuing thread busy for about as long as the
-        // MMAs run, so one thread's barrier waits and bookkeeping would leave the
-        // tensor pipe idle between stages.  Two issuers take alternate accumulation
-        // windows (TMEM buffer 0 and 1), so one waits while the other's MMAs run.
-        if (lane == 0) {
-            const int par = warp == 1 ? 0 : 1;
-            const uint32_t idesc = make_idesc(128, a.n_tile);
-            const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
-            bool ok = true;
-            for (int win = par; win < nwin && ok; win += 2) {
-                const int b = win & 1;
-                if (win >= 2 &&
-                    !mbar_wait(&drained[b], (uint32_t)((win - 2) >> 1) & 1u, abort_flag, a.status, a.wait_limit))
-                    break;
-                const int it1 = min((win + 1) * PROMOTE, a.kstages);
-                for (int it = win * PROMOTE; it < it1; ++it) {
+    if (warp < AGEN_WARP0) {
+        regs_dec<REG_CTRL>();
+        if (warp == 0) {
+            // ------------------------------------------------------ TMA producer
+            if (lane == 0) {
+                // a stage's lines are requested into L2 a few stages before its copy is issued
+                auto prefetch = [&](int it) {
+                    bulk_prefetch(a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2));
+                    tma_prefetch_2d(&mb0, it * KSTEP, n0);
+                    tma_prefetch_2d(&mb1, it * KSTEP, n0);
+                    if (!a.src_from_b) {
+                        tma_prefetch_2d(&ms0, it * KSTEP, gb * GBLK);
+                        tma_prefetch_2d(&ms1, it * KSTEP, gb * GBLK);
+                    }
+                };
+                for (int it = 0; it < PREFETCH && it < a.kstages; ++it) prefetch(it);
+                int last = -1;
+                // with copies withheld (fault injection for tests) nothing is issued, so the
+                // consumers' first waits run out and the kernel reports a timeout
+                for (int it = 0; it < (a.withhold ? 0 : a.kstages); ++it) {
                     const int s = it % NSTAGE;
-                    const bool first = it == win * PROMOTE;
-                    // the A warps arrive only after they saw this stage's copies land
-                    if (!mbar_wait(&full_a[it % (2 * NSTAGE)], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag,
-                                   a.status, a.wait_limit)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
+                    const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+                    if (it + PREFETCH < a.kstages) prefetch(it + PREFETCH);
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, a.status, a.wait_limit)) break;
+                    uint64_t* fb = &full_b[it % (2 * NSTAGE)];
                     unsigned char* st = base + s * stage_bytes;
-                    const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes, b2 = b1 + bbytes;
-                    const uint32_t d = tmem + (uint32_t)b * a.acc_off;
-                    const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE, a2 = a1 + ATILE;
-#pragma unroll
-                    for (int kk = 0; kk < KSTEP / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc, (first && kk == 0) ? 0u : 1u);
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
-                        umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                    mbar_arrive_tx(fb, NPB * bbytes + sbytes + TPS * (uint32_t)sizeof(float2));
+                    bulk_load(Wbuf + s * TPS, a.wtab + (size_t)iw * a.wld + (size_t)it * TPS, TPS * sizeof(float2),
+                              fb);
+                    tma_load_2d(st, &mb0, fb, it * KSTEP, n0);
+                    tma_load_2d(st + bbytes, &mb1, fb, it * KSTEP, n0);
+                    if (!a.src_from_b) {
+                        unsigned char* sp = st + NPB * bbytes;
+                        tma_load_2d(sp, &ms0, fb, it * KSTEP, gb * GBLK);
+                        tma_load_2d(sp + spiece, &ms1, fb, it * KSTEP, gb * GBLK);
                     }
-                    umma_commit(&empty[s]);
+                    last = it;
                 }
-                if (ok) umma_commit(&acc_full[b]);
+                // let every copy still in flight (at most the last NSTAGE stages) land before the CTA can exit
+                for (int it = max(0, last - NSTAGE + 1); it <= last; ++it)
+                    mbar_wait(&full_b[it % (2 * NSTAGE)], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag, a.status,
+                              CLEANUP_WAIT_LIMIT, false);
             }
-            // no MMA of either issuer may still be running when TMEM is freed (also on the abort path)
-            umma_commit(mma_done);
-            mbar_wait(mma_done, 0, abort_flag, a.status, CLEANUP_WAIT_LIMIT, false);
+        } else if (warp == 1 || warp == MMA_WARP2) {
+            // ------------------------------------------------------ MMA issuers
+            // Issuing tcgen05.mma keeps the issuing thread busy for about as long as the
+            // MMAs run, so one thread's barrier waits and bookkeeping would leave the
+            // tensor pipe idle between stages.  Two issuers take alternate accumulation
+            // windows (TMEM buffer 0 and 1), so one waits while the other's MMAs run.
+            if (lane == 0) {
+                const int par = warp == 1 ? 0 : 1;
+                const uint32_t idesc = make_idesc(128, a.n_tile);
+                bool ok = true;
+                for (int win = par; win < nwin && ok; win += 2) {
+                    const int b = win & 1;
+                    if (win >= 2 &&
+                        !mbar_wait(&drained[b], (uint32_t)((win - 2) >> 1) & 1u, abort_flag, a.status, a.wait_limit))
+                        break;
+                    const int it1 = min((win + 1) * PROMOTE, a.kstages);
+                    for (int it = win * PROMOTE; it < it1; ++it) {
+                        const int s = it % NSTAGE;
+                        const bool first = it == win * PROMOTE;
+                        // the A warps arrive only after they saw this stage's copies land
+                        if (!mbar_wait(&full_a[it % (2 * NSTAGE)], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag,
+                                       a.status, a.wait_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        unsigned char* st = base + s * stage_bytes;
+                        const uint32_t b0 = smem_u32(st), b1 = b0 + bbytes;
+                        const uint32_t d = tmem + (uint32_t)b * a.acc_off;
+                        const uint32_t a0 = smem_u32(st + aoff), a1 = a0 + ATILE, a2 = a1 + ATILE;
+#pragma unroll
+                        for (int kk = 0; kk < KSTEP / 16; ++kk) {
+                            const uint32_t off = kk * 32;
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b0 + off), idesc,
+                                      (first && kk == 0) ? 0u : 1u);
+                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
+                            umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
+                        }
+                        umma_commit(&empty[s]);
+                    }
+                    if (ok) umma_commit(&acc_full[b]);
+                }
+                // no MMA of either issuer may still be running when TMEM is freed (also on the abort path)
+                umma_commit(mma_done);
+                mbar_wait(mma_done, 0, abort_flag, a.status, CLEANUP_WAIT_LIMIT, false);
+            }
         }
-    } else if (warp < MMA_WARP2) {
-        // --------------------------------- A generation, accumulator drain, epilogue
-        const int wi = warp - 2;            // 0..7
-        const int g = threadIdx.x - 64;     // 0..255
-        const int j = g & 3;                // 16-byte chunk = 4 transitions
-        const int go = g >> 2;              // G' offset in the block (0..63)
+    } else if (warp < DRAIN_WARP0) {
+        regs_dec<REG_AGEN>();
+        // ------------------------------------------------------------ A generation
+        const int g = threadIdx.x - 32 * AGEN_WARP0;   // 0..255
+        const int j = g & 3;                           // 16-byte chunk = 4 transitions
+        const int go = g >> 2;                         // G' offset in the block (0..63)
         const int Gp = gb * GBLK + go;
-        // drain mapping: lane quadrant q, column half hc
-        const int q = warp & 3, hc = wi >> 2;
-        const int half = a.n_tile >> 1;
-        const int nch8 = half >> 3;         // 8-column TMEM loads per thread
-        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        const int row = q * 32 + lane;      // accumulator row: 0..63 re, 64..127 im
-        double* acc64 = a.acc64 + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 + row) * a.n_tile + hc * half;
-        const int nwin = (a.kstages + PROMOTE - 1) / PROMOTE;
-        float part[MAXHALF];
-#pragma unroll
-        for (int i = 0; i < MAXHALF; ++i) part[i] = 0.0f;
-        bool ok = true;
-        int flushed = 0;                    // FP64 region initialised?
-
-        auto drain = [&](int wd) -> bool {
-            const int b = wd & 1;
-            if (!warp_wait(&acc_full[b], (uint32_t)(wd >> 1) & 1u, abort_flag, a.status, a.wait_limit)) return false;
-            tc_fence_after();
-            const uint32_t tb = tmem + lane_off + (uint32_t)b * a.acc_off + (uint32_t)(hc * half);
-            // 8-column loads in pairs, one wait per pair (compile-time register indices)
-#pragma unroll
-            for (int grp = 0; grp < MAXHALF / 16; ++grp) {
-                uint32_t r[2][8];
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-                    if (grp * 2 + u < nch8) tmem_ld8(tb + (uint32_t)((grp * 2 + u) * 8), r[u]);
-                tmem_wait_ld();
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-                    if (grp * 2 + u < nch8) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) part[(grp * 2 + u) * 8 + i] += __uint_as_float(r[u][i]);
-                    }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&drained[b]);
-            if (((wd + 1) * PROMOTE) % FLUSH == 0 || wd + 1 == nwin) {
-#pragma unroll
-                for (int c = 0; c < MAXHALF; ++c) {
-                    if (c < half) {
-                        acc64[c] = (flushed ? acc64[c] : 0.0) + (double)part[c];
-                        part[c] = 0.0f;
-                    }
-                }
-                flushed = 1;
-            }
-            return true;
-        };
-
-        for (int it = 0; it < a.kstages && ok; ++it) {
+        for (int it = 0; it < a.kstages; ++it) {
             const int s = it % NSTAGE;
             const int s2 = it % (2 * NSTAGE);
             // the producer issued this stage's copies only after the MMAs of its previous use
             // finished, so a landed stage is also free to overwrite
-            if (!(ok = warp_wait(&full_b[s2], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag, a.status,
-                                 a.wait_limit)))
+            if (!warp_wait(&full_b[s2], (uint32_t)(it / (2 * NSTAGE)) & 1u, abort_flag, a.status, a.wait_limit))
                 break;
             unsigned char* st = base + s * stage_bytes;
-            const unsigned char* srcb = a.src_from_b ? st : st + NPIECE * bbytes;
+            const unsigned char* srcb = a.src_from_b ? st : st + NPB * bbytes;
             const uint32_t src_piece = a.src_from_b ? bbytes : spiece;
             uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};   // re row
             uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0}, im2[4] = {0, 0, 0, 0};   // im row
@@ -293,17 +261,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t coff = sw64_off(srow, j);
                 const uint4 h0 = *reinterpret_cast<const uint4*>(srcb + coff);
                 const uint4 h1 = *reinterpret_cast<const uint4*>(srcb + src_piece + coff);
-                const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
-                const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
-                               v2[4] = {h2.x, h2.y, h2.z, h2.w};
+                const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w};
                 const float4* Wv4 = reinterpret_cast<const float4*>(Wbuf + s * TPS + 4 * j);
                 const float4 wa = Wv4[0], wb = Wv4[1];
                 const float2 Wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
                                       make_float2(wb.z, wb.w)};
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
-                    const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
-                    const float rr = f0.x + (f1.x + f2.x), ri = f0.y + (f1.y + f2.y);
+                    // rho~ = b0 + b1 is exact in FP32 (16 significant bits)
+                    const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]);
+                    const float rr = f0.x + f1.x, ri = f0.y + f1.y;
                     const float2 wq = Wv[qq];
                     const float xr = wq.x * rr - wq.y * ri;
                     const float xi = wq.x * ri + wq.y * rr;
@@ -325,12 +292,69 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_a[s2]);
-            // drain the previous window once this window's A tiles are all queued (its
-            // MMAs finished long ago, so the drain does not wait on the tensor pipe)
-            if (it % PROMOTE == PROMOTE - 1 && it >= PROMOTE && !(ok = drain(it / PROMOTE - 1))) break;
         }
-        if (ok && nwin >= 2 && (a.kstages - 1) % PROMOTE != PROMOTE - 1) ok = drain(nwin - 2);
-        if (ok) ok = drain(nwin - 1);
+    } else {
+        regs_inc<REG_DRAIN>();
+        // ---------------------------------------------- accumulator drain and epilogue
+        const int wi = warp - DRAIN_WARP0;  // 0..7
+        // TMEM lane quadrant q (a warp reads the lanes 32 (warp mod 4) ..), column half hc
+        const int q = warp & 3, hc = wi >> 2;
+        const int half = a.n_tile >> 1;
+        const int nch16 = half >> 4;        // 16-column TMEM loads per thread (half is a multiple of 8)
+        const bool tail8 = (half & 15) != 0;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int row = q * 32 + lane;      // accumulator row: 0..63 re, 64..127 im
+        double* acc64 = a.acc64 + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 + row) * a.n_tile + hc * half;
+        float part[MAXHALF];
+#pragma unroll
+        for (int i = 0; i < MAXHALF; ++i) part[i] = 0.0f;
+        bool ok = true;
+        int flushed = 0;                    // FP64 region initialised?
+        for (int wd = 0; wd < nwin && ok; ++wd) {
+            const int b = wd & 1;
+            if (!(ok = warp_wait(&acc_full[b], (uint32_t)(wd >> 1) & 1u, abort_flag, a.status, a.wait_limit))) break;
+            tc_fence_after();
+            const uint32_t tb = tmem + lane_off + (uint32_t)b * a.acc_off + (uint32_t)(hc * half);
+            // two 16-column loads in flight per wait (compile-time register indices)
+#pragma unroll
+            for (int grp = 0; grp < MAXHALF / 32; ++grp) {
+                uint32_t r[2][16];
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (grp * 2 + u < nch16) tmem_ld16(tb + (uint32_t)((grp * 2 + u) * 16), r[u]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (grp * 2 + u < nch16) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) part[(grp * 2 + u) * 16 + i] += __uint_as_float(r[u][i]);
+                    }
+            }
+            if (tail8) {                    // the last 8 columns of a half that is not a multiple of 16
+                uint32_t r8[8];
+                tmem_ld8(tb + (uint32_t)(nch16 * 16), r8);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < MAXHALF; c += 8)
+                    if (c == nch16 * 16) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) part[c + i] += __uint_as_float(r8[i]);
+                    }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&drained[b]);
+            if (((wd + 1) * PROMOTE) % FLUSH == 0 || wd + 1 == nwin) {
+#pragma unroll
+                for (int c = 0; c < MAXHALF; ++c) {
+                    if (c < half) {
+                        acc64[c] = (flushed ? acc64[c] : 0.0) + (double)part[c];
+                        part[c] = 0.0f;
+                    }
+                }
+                flushed = 1;
+            }
+        }
         // -------------------------------------------------------------- epilogue
         if (ok) {
             const int cpart = row >> 6, gro = row & 63;
@@ -390,17 +414,20 @@ __global__ void k_weights(int nw, long long ld, long long nt, int nv, int nc, co
 // there Im chi0_GG is formed from products of size |Re W| |rho|^2 that cancel to
 // |Im W| |rho|^2, so the split's 2^-24 is amplified by |w - dE|/eta far from resonance.
 // Here chi0_GG(w) = pref sum_t W_t(w) |rho_t(G)|^2 with |rho|^2 formed first (FP32 rho as
-// the sum of its three BF16 terms), FP32 sums over 256 transitions added in FP64; eps_GG =
-// 1 - v(G) chi0_GG is rewritten (and the chi0 diagonal, if kept).  CTA: 32 w x 32 G, thread
-// 2 x 2; transitions staged 32 at a time.
-__global__ void __launch_bounds__(256) k_diag_chi(int nw, int ng, long long nt, const float2* W, long long wld,
-                                                  const __nv_bfloat162* p0, const __nv_bfloat162* p1,
-                                                  const __nv_bfloat162* p2, long long kp2, double pref,
-                                                  const double* vs, double2* eps, double2* chi) {
+// the sum of its three BF16 terms), FP32 sums over 256 transitions added in FP64.  The
+// transitions are split into gridDim.z ranges of tps (a multiple of 256) so that the
+// launch fills the GPU; each CTA (32 w x 32 G, thread 2 x 2, transitions staged 32 at a
+// time) writes its range's FP64 sums to part[z][w][G], and k_diag_finish adds the ranges
+// in a fixed order.
+__global__ void __launch_bounds__(256) k_diag_chi(int nw, int ng, long long nt, long long tps, const float2* W,
+                                                  long long wld, const __nv_bfloat162* p0,
+                                                  const __nv_bfloat162* p1, const __nv_bfloat162* p2,
+                                                  long long kp2, double2* part) {
     __shared__ float2 Ws[32][33];            // [t][w]
     __shared__ float Rs[32][33];             // [t][G]
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int G0 = blockIdx.x * 32, w0 = blockIdx.y * 32;
+    const long long tb = (long long)blockIdx.z * tps, te = min(nt, tb + tps);
     float2 acc[2][2];
     double2 acc64[2][2];
 #pragma unroll
@@ -411,7 +438,7 @@ __global__ void __launch_bounds__(256) k_diag_chi(int nw, int ng, long long nt, 
             acc64[i][j] = make_double2(0.0, 0.0);
         }
     int chunk = 0;
-    for (long long t0 = 0; t0 < nt; t0 += 32) {
+    for (long long t0 = tb; t0 < te; t0 += 32) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int i = threadIdx.x + 256 * r;
@@ -419,7 +446,7 @@ __global__ void __launch_bounds__(256) k_diag_chi(int nw, int ng, long long nt, 
             const long long t = t0 + tt;
             float2 wv = make_float2(0.f, 0.f);
             float rv = 0.f;
-            if (t < nt) {
+            if (t < te) {
                 if (w0 + row < nw) wv = W[(long long)(w0 + row) * wld + t];
                 if (G0 + row < ng) {
                     const long long o = (long long)(G0 + row) * kp2 + t;
@@ -447,7 +474,7 @@ __global__ void __launch_bounds__(256) k_diag_chi(int nw, int ng, long long nt, 
             acc[1][1].y = fmaf(wb.y, rb, acc[1][1].y);
         }
         __syncthreads();
-        if (++chunk == 8 || t0 + 32 >= nt) {
+        if (++chunk == 8 || t0 + 32 >= te) {
             chunk = 0;
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -464,13 +491,28 @@ __global__ void __launch_bounds__(256) k_diag_chi(int nw, int ng, long long nt, 
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int w = w0 + ty + 16 * i, G = G0 + tx + 16 * j;
-            if (w >= nw || G >= ng) continue;
-            const double2 ch = make_double2(pref * acc64[i][j].x, pref * acc64[i][j].y);
-            const double vv = vs[G] * vs[G];
-            const size_t o = ((size_t)w * ng + G) * ng + G;
-            eps[o] = make_double2(1.0 - vv * ch.x, -vv * ch.y);
-            if (chi) chi[o] = ch;
+            if (w < nw && G < ng) part[((size_t)blockIdx.z * nw + w) * ng + G] = acc64[i][j];
         }
+}
+
+// eps_GG = 1 - v(G) chi0_GG from the ranges' sums (added in range order), and the chi0
+// diagonal if it is kept; one thread per (w, G).
+__global__ void k_diag_finish(int nw, int ng, int nsplit, const double2* part, double pref, const double* vs,
+                              double2* eps, double2* chi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nw * ng) return;
+    const int w = i / ng, G = i - w * ng;
+    double2 sum = make_double2(0.0, 0.0);
+    for (int z = 0; z < nsplit; ++z) {
+        const double2 v = part[(size_t)z * nw * ng + i];
+        sum.x += v.x;
+        sum.y += v.y;
+    }
+    const double2 ch = make_double2(pref * sum.x, pref * sum.y);
+    const double vv = vs[G] * vs[G];
+    const size_t o = ((size_t)w * ng + G) * ng + G;
+    eps[o] = make_double2(1.0 - vv * ch.x, -vv * ch.y);
+    if (chi) chi[o] = ch;
 }
 
 }  // namespace
@@ -543,8 +585,8 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     if (a.n_tile > 2 * MAXHALF || a.n_tile < 16) return cudaErrorNotSupported;
 
     const uint32_t bbytes = (uint32_t)a.n_tile * ROWB;
-    const uint32_t sbytes = a.src_from_b ? 0u : NPIECE * GBLK * ROWB;
-    const size_t stage_bytes = NPIECE * bbytes + sbytes + NPIECE * ATILE;
+    const uint32_t sbytes = a.src_from_b ? 0u : NPB * GBLK * ROWB;
+    const size_t stage_bytes = NPB * bbytes + sbytes + NPA * ATILE;
     const size_t smem = 1024 + NSTAGE * stage_bytes + NSTAGE * (KSTEP / 2) * sizeof(float2) +
                         (5 * NSTAGE + 5) * sizeof(uint64_t) + 16;
     if (smem > SMEM_LIMIT) return cudaErrorNotSupported;
@@ -562,27 +604,46 @@ cudaError_t qcx_launch_chi0_mixed(qcx_ctx* ctx, QSlot& s, int iq, double2* chi, 
     }
     a.wtab = s.wtab.as<float2>();
     dim3 grid(a.n_gb * s.nw, n_chunks);
-    const size_t acc_bytes = (size_t)grid.x * grid.y * 128 * a.n_tile * sizeof(double);
+    // split of the transitions for the diagonal pass: enough CTAs to fill the GPU, each range a
+    // multiple of 256 transitions; its partial sums reuse acc64 once k_chi0_tc has finished
+    const dim3 dgrid((ng + 31) / 32, (s.nw + 31) / 32);
+    const long long want = std::max<long long>(1, (8LL * 152 + dgrid.x * dgrid.y - 1) / (dgrid.x * dgrid.y));
+    const long long tps = std::max<long long>(256, ((nt + want - 1) / want + 255) / 256 * 256);
+    const int nsplit = (int)((nt + tps - 1) / tps);
+    const size_t acc_bytes = std::max((size_t)grid.x * grid.y * 128 * a.n_tile * sizeof(double),
+                                      (size_t)nsplit * s.nw * ng * sizeof(double2));
     e = s.acc64.ensure(acc_bytes);
     if (e != cudaSuccess) return e;
     a.acc64 = s.acc64.as<double>();
 
     unsigned char* p0 = reinterpret_cast<unsigned char*>(s.rho.p);
     const size_t plane = (size_t)s.ngp * s.kp * 2;
-    CUtensorMap mb[3], ms[3];
-    for (int i = 0; i < 3; ++i)
+    CUtensorMap mb[NPB], ms[NPB];
+    for (int i = 0; i < NPB; ++i)
         if (!qcx_make_bf16_map(&mb[i], p0 + i * plane, s.kp, s.ngp, a.n_tile, KSTEP) ||
             !qcx_make_bf16_map(&ms[i], p0 + i * plane, s.kp, s.ngp, GBLK, KSTEP))
             return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute((const void*)k_chi0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_chi0_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mb[0], mb[1], mb[2], ms[0], ms[1], ms[2], a);
+    {
+        // the warpgroups' register budgets assume this launch allocation; another one could leave a
+        // setmaxnreg.inc waiting for registers that no warpgroup gives back
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, (const void*)k_chi0_tc);
+        if (e != cudaSuccess) return e;
+        if (fa.numRegs != LAUNCH_REGS) return cudaErrorNotSupported;
+    }
+    k_chi0_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mb[0], mb[1], ms[0], ms[1], a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const __nv_bfloat162* q0 = reinterpret_cast<const __nv_bfloat162*>(s.rho.p);
     const long long plane2 = (long long)s.ngp * (s.kp / 2);
-    k_diag_chi<<<dim3((ng + 31) / 32, (s.nw + 31) / 32), 256, 0, ctx->stream>>>(
-        s.nw, ng, nt, s.wtab.as<float2>(), s.kp / 2, q0, q0 + plane2, q0 + 2 * plane2, s.kp / 2, a.pref,
-        s.vs.as<double>(), s.eps.as<double2>(), chi);
+    double2* part = s.acc64.as<double2>();
+    k_diag_chi<<<dim3(dgrid.x, dgrid.y, nsplit), 256, 0, ctx->stream>>>(
+        s.nw, ng, nt, tps, s.wtab.as<float2>(), s.kp / 2, q0, q0 + plane2, q0 + 2 * plane2, s.kp / 2, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_diag_finish<<<(s.nw * ng + 255) / 256, 256, 0, ctx->stream>>>(s.nw, ng, nsplit, part, a.pref,
+                                                                     s.vs.as<double>(), s.eps.as<double2>(), chi);
     return cudaGetLastError();
 }

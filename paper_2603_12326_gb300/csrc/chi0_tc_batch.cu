@@ -5,8 +5,11 @@
 // The arithmetic per tile is that of the per-q kernel: one 64-row G' block
 // of one instance at its frequency (a 128 x N accumulator: 64 re rows and 64
 // im rows of chi0_GG'), one N chunk of its G list, the contraction over
-// k' = 2t + p split into three BF16 terms with the six products of order <= 2,
-// FP32 accumulation restarted after 24 MMAs (two K stages) and promoted
+// k' = 2t + p with B = rho~ = b0 + b1 (the first two BF16 terms of the FP32 pair
+// densities) and A = W rho~ in three BF16 terms, the five products
+// a0 b0 + a0 b1 + a1 b0 + a1 b1 + a2 b0 (both sides carry the same rho~, so only
+// A's split and the dropped a2 b1 are errors of the contraction),
+// FP32 accumulation restarted after 20 MMAs (two K stages) and promoted
 // through FP32 registers into an FP64 buffer, and eps = delta - v^1/2 chi0 v^1/2
 // written in FP64 (row G', column G).
 //
@@ -30,15 +33,16 @@ namespace {
 
 constexpr int NTHREADS = 384;             // warps: 0 TMA, 1 and 10 MMA, 2-9 A/drain/epilogue, 11 idle
 constexpr int MMA_WARP2 = 10;
-constexpr int NSTAGE = 3;
-constexpr int NPIECE = 3;
+constexpr int NSTAGE = 4;
+constexpr int NPA = 3;                    // BF16 terms of the A operand (W rho~)
+constexpr int NPB = 2;                    // BF16 terms of the B operand (rho~ = b0 + b1)
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per tile, rows per TMA box
 constexpr int MAXHALF = 96;
 constexpr int NMAX = 2 * MAXHALF;         // largest N of a tile
 constexpr int BREG = NMAX * ROWB;         // one B piece region
 constexpr int SPIECE = GBLK * ROWB;       // one A-source piece
-constexpr int STAGE_BYTES = NPIECE * BREG + NPIECE * SPIECE + NPIECE * ATILE;
+constexpr int STAGE_BYTES = NPB * BREG + NPB * SPIECE + NPA * ATILE;
 constexpr int TPS = KSTEP / 2;            // transitions per stage
 constexpr uint32_t ACC_OFF = 256;         // second TMEM buffer
 constexpr uint32_t TMEM_COLS = 512;
@@ -48,7 +52,7 @@ constexpr size_t SMEM_BYTES =
 static_assert(SMEM_BYTES <= (size_t)SMEM_LIMIT, "stage ring does not fit in shared memory");
 
 struct MapSet {
-    CUtensorMap m[QCX_BATCH_MAXQ][NPIECE];
+    CUtensorMap m[QCX_BATCH_MAXQ][NPB];
 };
 
 struct BArgs {
@@ -63,7 +67,7 @@ struct BArgs {
     double2* eps;
     int* status;
     long long wait_limit;     // clock cycles before a pipeline wait gives up
-    int promote;              // K stages per accumulation window (24 MMAs)
+    int promote;              // K stages per accumulation window (20 MMAs)
     int flush;                // K stages between FP64 flushes (64 windows)
 };
 
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                 const int nN = tl.w & 0xFFFF, src_b = tl.w >> 16;
                 const int slot = a.inst[tl.x].slot - a.slot0;
                 const int nbox = (nN + GBLK - 1) / GBLK;
-                const uint32_t bytes = (uint32_t)(NPIECE * nbox * GBLK * ROWB + (src_b ? 0 : NPIECE * SPIECE) +
+                const uint32_t bytes = (uint32_t)(NPB * nbox * GBLK * ROWB + (src_b ? 0 : NPB * SPIECE) +
                                                   TPS * (int)sizeof(float2));
                 const float2* wrow = a.wtab + (size_t)tl.x * a.wld;
                 for (int it = 0; it < a.kstages; ++it, ++gs) {
@@ -133,13 +137,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                     uint64_t* fb = &full_b[gs % (2 * NSTAGE)];
                     mbar_arrive_tx(fb, bytes);
                     bulk_load(Wbuf + s * TPS, wrow + (size_t)it * TPS, TPS * sizeof(float2), fb);
-                    for (int p = 0; p < NPIECE; ++p)
+                    for (int p = 0; p < NPB; ++p)
                         for (int r = 0; r < nbox; ++r)
                             tma_load_2d(st + p * BREG + r * SPIECE, &maps.m[slot][p], fb, it * KSTEP,
                                         tl.z + r * GBLK);
                     if (!src_b) {
-                        unsigned char* sp = st + NPIECE * BREG;
-                        for (int p = 0; p < NPIECE; ++p)
+                        unsigned char* sp = st + NPB * BREG;
+                        for (int p = 0; p < NPB; ++p)
                             tma_load_2d(sp + p * SPIECE, &maps.m[slot][p], fb, it * KSTEP, tl.y * GBLK);
                     }
                     last = gs;
@@ -181,9 +185,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                         }
                         tc_fence_after();
                         unsigned char* st = base + s * STAGE_BYTES;
-                        const uint32_t b0 = smem_u32(st), b1 = b0 + BREG, b2 = b1 + BREG;
+                        const uint32_t b0 = smem_u32(st), b1 = b0 + BREG;
                         const uint32_t d = tmem + (uint32_t)b * ACC_OFF;
-                        const uint32_t a0 = smem_u32(st + NPIECE * BREG + NPIECE * SPIECE), a1 = a0 + ATILE,
+                        const uint32_t a0 = smem_u32(st + NPB * BREG + NPB * SPIECE), a1 = a0 + ATILE,
                                        a2 = a1 + ATILE;
 #pragma unroll
                         for (int kk = 0; kk < KSTEP / 16; ++kk) {
@@ -192,7 +196,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                                       (first && kk == 0) ? 0u : 1u);
                             umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b1 + off), idesc, 1u);
                             umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b0 + off), idesc, 1u);
-                            umma_bf16(d, sw64_desc(a0 + off), sw64_desc(b2 + off), idesc, 1u);
                             umma_bf16(d, sw64_desc(a1 + off), sw64_desc(b1 + off), idesc, 1u);
                             umma_bf16(d, sw64_desc(a2 + off), sw64_desc(b0 + off), idesc, 1u);
                         }
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                                      a.wait_limit)))
                     break;
                 unsigned char* st = base + s * STAGE_BYTES;
-                const unsigned char* srcb = st + (src_b ? 0 : NPIECE * BREG);
+                const unsigned char* srcb = st + (src_b ? 0 : NPB * BREG);
                 const uint32_t src_piece = src_b ? (uint32_t)BREG : (uint32_t)SPIECE;
                 uint32_t re0[4] = {0, 0, 0, 0}, re1[4] = {0, 0, 0, 0}, re2[4] = {0, 0, 0, 0};
                 uint32_t im0[4] = {0, 0, 0, 0}, im1[4] = {0, 0, 0, 0}, im2[4] = {0, 0, 0, 0};
@@ -288,17 +291,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                     const uint32_t coff = sw64_off(row0 + go, j);
                     const uint4 h0 = *reinterpret_cast<const uint4*>(srcb + coff);
                     const uint4 h1 = *reinterpret_cast<const uint4*>(srcb + src_piece + coff);
-                    const uint4 h2 = *reinterpret_cast<const uint4*>(srcb + 2 * src_piece + coff);
-                    const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w},
-                                   v2[4] = {h2.x, h2.y, h2.z, h2.w};
+                    const uint32_t v0[4] = {h0.x, h0.y, h0.z, h0.w}, v1[4] = {h1.x, h1.y, h1.z, h1.w};
                     const float4* Wv4 = reinterpret_cast<const float4*>(Wbuf + s * TPS + 4 * j);
                     const float4 wa = Wv4[0], wb = Wv4[1];
                     const float2 Wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
                                           make_float2(wb.z, wb.w)};
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
-                        const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]), f2 = bf2(v2[qq]);
-                        const float rr = f0.x + (f1.x + f2.x), ri = f0.y + (f1.y + f2.y);
+                        // rho~ = b0 + b1 is exact in FP32 (16 significant bits)
+                        const float2 f0 = bf2(v0[qq]), f1 = bf2(v1[qq]);
+                        const float rr = f0.x + f1.x, ri = f0.y + f1.y;
                         const float2 wq = Wv[qq];
                         split3(wq.x * rr - wq.y * ri, wq.x * ri + wq.y * rr, re0[qq], re1[qq], re2[qq]);
                         // (xi, -xr) splits into the terms of (xr, xi), swapped, the second negated
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                         im2[qq] = perm_im(re2[qq]);
                     }
                 }
-                unsigned char* ap = st + NPIECE * BREG + NPIECE * SPIECE;
+                unsigned char* ap = st + NPB * BREG + NPB * SPIECE;
                 const uint32_t o_re = sw64_off(go, j), o_im = sw64_off(64 + go, j);
                 *reinterpret_cast<uint4*>(ap + o_re) = make_uint4(re0[0], re0[1], re0[2], re0[3]);
                 *reinterpret_cast<uint4*>(ap + ATILE + o_re) = make_uint4(re1[0], re1[1], re1[2], re1[3]);
@@ -371,7 +373,7 @@ cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, i
     MapSet ms;
     memset(&ms, 0, sizeof(ms));
     for (int s = 0; s < nslot; ++s)
-        for (int p = 0; p < NPIECE; ++p) ms.m[s][p] = maps[NPIECE * s + p];
+        for (int p = 0; p < NPB; ++p) ms.m[s][p] = maps[3 * s + p];   // the first two of each slot's three planes
     BArgs a;
     a.ntile = ntile;
     a.kstages = kstages;
@@ -385,7 +387,7 @@ cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, i
     a.eps = eps;
     a.status = status;
     a.wait_limit = wait_limit;
-    a.promote = 24 / ((KSTEP / 16) * 6);      // 24 MMAs per window: two K stages of twelve
+    a.promote = 2;                            // 20 MMAs per window: two K stages of ten
     a.flush = 64 * a.promote;
     cudaError_t e =
         cudaFuncSetAttribute((const void*)k_chi0_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);

@@ -3,9 +3,10 @@
 A random-schedule model of the roles of k_chi0_tc (one tile per CTA) and of
 the persistent k_chi0_tc_batch (a list of tiles per CTA, stage and window
 counters running on across tiles): the TMA producer, every A-operand warp
-(which also drains the accumulators; eight warps that all take every K stage,
-or, as a layout the model also checks, groups of four warps taking every
-fourth stage), two MMA issuers on alternate accumulation windows, copies that
+(eight warps that all take every K stage; in the batch kernel they also drain
+the accumulators, in the per-q kernel eight separate warps drain them; groups
+of four warps taking every fourth stage are a layout the model also checks),
+two MMA issuers on alternate accumulation windows, copies that
 land in any order and MMAs that complete in issue order.  A barrier completes
 a phase when its expected number of arrivals is in (each A warp arrives on its
 own), and a wait on parity p returns once the completed-phase count's parity
@@ -17,7 +18,7 @@ and that when the producer leaves no copy is in flight and when TMEM is freed
 no MMA is.  The same model runs with waits that give up (a wait limit that
 runs out, or copies withheld so that nothing completes): the abort must still
 end every role with its copies landed and its MMAs finished.  Ring depth and
-window length are read from the kernel sources (three stages, windows of two
+window length are read from the kernel sources (four stages, windows of two
 for both kernels).  The copy and A-tile barriers are indexed by the stage
 modulo (number of A groups, at least two) x ring depth, so a barrier's
 previous phase always belongs to the same A-warp group and lies two windows
@@ -57,12 +58,13 @@ class _Bar:
         return (self.done & 1) != parity
 
 
-def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, withhold=False):
-    """One random schedule.  ngroups = 4: the per-q kernel (16 A warps in groups
-    of four, group g forms stages g, g+4, ...; a warp drains the windows before
-    wd after its group's last stage of window wd); ngroups = 1: the batch kernel
-    (8 A warps, every stage; the previous window is drained after a window's
-    last stage)."""
+def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, withhold=False, drain_warps=0):
+    """One random schedule.  ngroups = 4: 16 A warps in groups of four, group g
+    forms stages g, g+4, ...; a warp drains the windows before wd after its
+    group's last stage of window wd; ngroups = 1: 8 A warps, every stage; with
+    drain_warps = 0 (the batch kernel) they drain the previous window after a
+    window's last stage, with drain_warps = n (the per-q kernel) n other warps
+    drain every window in order and the A warps only form A tiles."""
     rnd = random.Random(seed)
     wpg = 4 if ngroups > 1 else 8                 # warps per group
     nwarp = wpg * ngroups
@@ -71,7 +73,8 @@ def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, wit
     full_a = [_Bar(wpg) for _ in range(nb)]
     empty = [_Bar(1) for _ in range(nstage)]
     acc_full = [_Bar(1), _Bar(1)]
-    drained = [_Bar(nwarp), _Bar(nwarp)]
+    ndrain = drain_warps or nwarp
+    drained = [_Bar(ndrain), _Bar(ndrain)]
     mma_done_bar = _Bar(2)
     landed, gen_done, mma_done, drain_done = set(), {}, set(), {}
     copies, mmas, errors = [], [], []
@@ -134,7 +137,9 @@ def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, wit
                     errors.append("A tile %d overwritten under its MMAs" % gs)
                 gen_done[gs] = gen_done.get(gs, 0) + 1
                 full_a[s].arrive()
-                if ngroups > 1:
+                if drain_warps:
+                    nxt = nwin
+                elif ngroups > 1:
                     wd = it // promote
                     if it + ngroups >= min((wd + 1) * promote, kstages):
                         while nxt < wd:
@@ -161,6 +166,15 @@ def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, wit
                 if not ok:
                     return
 
+    def drain_warp():
+        for gw in range(ntile * nwin):
+            ok = yield from wait(acc_full[gw & 1], (gw >> 1) & 1, lambda gw=gw: ("win", gw) in mma_done,
+                                 "window %d" % gw)
+            if not ok:
+                return
+            drain_done[gw] = drain_done.get(gw, 0) + 1
+            drained[gw & 1].arrive()
+
     def issuer(par):
         ok = True
         for lt in range(ntile):
@@ -171,7 +185,7 @@ def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, wit
                 b = gw & 1
                 if gw >= 2:
                     ok = yield from wait(drained[b], ((gw - 2) >> 1) & 1,
-                                         lambda g=gw: drain_done.get(g - 2, 0) == nwarp,
+                                         lambda g=gw: drain_done.get(g - 2, 0) == ndrain,
                                          "buffer of window %d drained" % gw)
                     if not ok:
                         break
@@ -194,6 +208,7 @@ def _run(kstages, nstage, promote, seed, ngroups=4, ntile=1, timeouts=False, wit
                         "every MMA finished", honour_abort=False)
 
     actors = [producer(), issuer(0), issuer(1)] + [a_warp(w) for w in range(nwarp)]
+    actors += [drain_warp() for _ in range(drain_warps)]
     alive = [True] * len(actors)
     for _ in range(2000000):
         if not any(alive):
@@ -228,12 +243,15 @@ def test_model_matches_the_kernel_sources():
     """The constants and counts the model assumes are those of the kernels."""
     for name in ("chi0_tc.cu", "chi0_tc_batch.cu"):
         src = _src(name)
-        assert _constant("NSTAGE", name) == 3, name
+        assert _constant("NSTAGE", name) == 4, name
         assert "mbar_init(&full_a[s], 8)" in src and "mbar_init(&drained[b], 8)" in src, name
         assert "mbar_init(&full_a[s + NSTAGE], 8)" in src, name
         assert src.count("% (2 * NSTAGE)") >= 4, name
+    # the per-q kernel: eight A warps (warps 4-11) and eight drain warps (12-19)
+    assert _constant("AGEN_WARP0", "chi0_tc.cu") == 4 and _constant("DRAIN_WARP0", "chi0_tc.cu") == 12
+    assert _constant("NTHREADS", "chi0_tc.cu") == 640
     assert _constant("PROMOTE", "chi0_tc.cu") == 2
-    assert "a.promote = 24 / ((KSTEP / 16) * 6)" in _src("chi0_tc_batch.cu")
+    assert "a.promote = 2;" in _src("chi0_tc_batch.cu")
     assert "for (int it = max(0, last - NSTAGE + 1); it <= last; ++it)" in _src("chi0_tc.cu")
 
 
@@ -241,22 +259,24 @@ def test_model_matches_the_kernel_sources():
 def test_kernel_protocol_holds_under_random_schedules(kstages):
     nstage, promote = _constant("NSTAGE", "chi0_tc.cu"), _constant("PROMOTE", "chi0_tc.cu")
     for seed in range(20):
-        errors, aborted = _run(kstages, nstage, promote, seed, ngroups=1)
+        errors, aborted = _run(kstages, nstage, promote, seed, ngroups=1, drain_warps=8)
         assert not errors and not aborted, (nstage, kstages, seed, errors[:3])
 
 
-@pytest.mark.parametrize("nstage,promote,ngroups", [(3, 2, 1), (4, 4, 4), (5, 4, 4), (7, 4, 4)])
-def test_kernel_abort_path_drains_copies_and_mmas(nstage, promote, ngroups):
+@pytest.mark.parametrize("nstage,promote,ngroups,drain_warps",
+                         [(4, 2, 1, 8), (3, 2, 1, 0), (4, 2, 1, 0), (4, 4, 4, 0), (5, 4, 4, 0), (7, 4, 4, 0)])
+def test_kernel_abort_path_drains_copies_and_mmas(nstage, promote, ngroups, drain_warps):
     """Waits that give up at random points (or copies withheld, so that the
     first waits run out): every role ends, the producer leaves no copy in
     flight and no MMA runs when TMEM is freed.  Also for rings of four A-warp
     groups (a layout the model keeps for comparison)."""
     n_abort = 0
     for seed in range(30):
-        errors, aborted = _run(24, nstage, promote, seed, ngroups=ngroups, timeouts=True)
+        errors, aborted = _run(24, nstage, promote, seed, ngroups=ngroups, timeouts=True, drain_warps=drain_warps)
         assert not errors, (seed, errors[:3])
         n_abort += bool(aborted)
-        errors, aborted = _run(9, nstage, promote, seed, ngroups=ngroups, timeouts=True, withhold=True)
+        errors, aborted = _run(9, nstage, promote, seed, ngroups=ngroups, timeouts=True, withhold=True,
+                               drain_warps=drain_warps)
         assert not errors and aborted, (seed, errors[:3])
     assert n_abort > 0
 
@@ -328,6 +348,15 @@ def _run_spec(kstages, nstage, promote, seed, timeouts=False, withhold=False):
                 return
             drain_done[wd] = drain_done.get(wd, 0) + 1
             drained[wd & 1].arrive()
+
+    def drain_warp():
+        for gw in range(ntile * nwin):
+            ok = yield from wait(acc_full[gw & 1], (gw >> 1) & 1, lambda gw=gw: ("win", gw) in mma_done,
+                                 "window %d" % gw)
+            if not ok:
+                return
+            drain_done[gw] = drain_done.get(gw, 0) + 1
+            drained[gw & 1].arrive()
 
     def issuer(par):
         ok = True

@@ -3,8 +3,9 @@ split-BF16 tcgen05 chi0 with FP32 accumulation, FP32 Gauss-Jordan inverse, the
 FP64 diagonal correction for ill-conditioned blocks and the loss as a quadratic
 form for the others) vs the FP64 CPU oracle.
 
-Tolerances follow from the arithmetic: three BF16 terms represent x to 2^-24
-relative and the six products kept miss terms of that order, so chi0 carries
+Tolerances follow from the arithmetic: the contraction takes rho~ (the first two
+BF16 terms of rho) on both sides, so its errors are W rho~'s three-term split
+(2^-24 relative) and the one product left out (of that order), and chi0 carries
 the FP32 rounding of its sums (5e-5 bound on its largest element); the inverse
 amplifies eps errors by its condition number.  The loss functions must stay within 1e-4 relative wherever they
 exceed 1e-3 of their per-q maximum (the bar the method is held to)."""
