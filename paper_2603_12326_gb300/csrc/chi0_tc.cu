@@ -28,7 +28,7 @@
 //
 // The tensor core's FP32 accumulation truncates, so long sums drift (about
 // 2^-24 of the running value per MMA, always toward zero).  The accumulator
-// is therefore restarted every PROMOTE K stages: TMEM holds two buffers used
+// is therefore restarted every PROMOTE K stages (40 MMAs): TMEM holds two buffers used
 // in turn, the finished buffer is drained into FP32 registers (round to
 // nearest), and every FLUSH stages the register partials are added into an
 // FP64 buffer owned by the CTA.  The Dyson step runs in FP64 from that
@@ -70,7 +70,7 @@ constexpr int NPA = 3;                    // BF16 terms of the A operand (W rho~
 constexpr int NPB = 2;                    // BF16 terms of the B operand (rho~ = b0 + b1)
 constexpr int ATILE = 128 * ROWB;         // one 128-row A piece
 constexpr int GBLK = 64;                  // G' rows per half tile
-constexpr int PROMOTE = 2;                // K stages accumulated in one TMEM buffer
+constexpr int PROMOTE = 4;                // K stages accumulated in one TMEM buffer (40 MMAs)
 constexpr int FLUSH = 128;                // stages between FP64 flushes of the register partials
 constexpr int MAXHALF = 96;               // columns of the accumulator one thread drains (n_tile/2)
 constexpr int SMEM_LIMIT = 232448;
@@ -85,7 +85,8 @@ struct TcArgs {
     long long wld;        // row length of wtab
     double pref;
     const double* vs;
-    double* acc64;    // [grid][128][n_tile] FP64 partial sums, one region per CTA
+    double* acc64;    // [grid][n_tile][128] FP64 partial sums, one region per CTA (column-major, so a
+                      // warp's 32 accumulator rows are contiguous)
     double2* eps;     // [nw][ng][ng], eps^T: row G', column G (FP64)
     double2* chi;     // optional [nw][ng][ng], row G, column G'
     int* status;
@@ -304,7 +305,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool tail8 = (half & 15) != 0;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const int row = q * 32 + lane;      // accumulator row: 0..63 re, 64..127 im
-        double* acc64 = a.acc64 + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 + row) * a.n_tile + hc * half;
+        double* acc64 = a.acc64 + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 128 * a.n_tile +
+                        (size_t)(hc * half) * 128 + row;
         float part[MAXHALF];
 #pragma unroll
         for (int i = 0; i < MAXHALF; ++i) part[i] = 0.0f;
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int c = 0; c < MAXHALF; ++c) {
                     if (c < half) {
-                        acc64[c] = (flushed ? acc64[c] : 0.0) + (double)part[c];
+                        acc64[(size_t)c * 128] = (flushed ? acc64[(size_t)c * 128] : 0.0) + (double)part[c];
                         part[c] = 0.0f;
                     }
                 }
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int col = 0; col < half; ++col) {
                     const int G = n0 + hc * half + col;
                     if (G < a.ng) {
-                        const double ch = a.pref * acc64[col];
+                        const double ch = a.pref * acc64[(size_t)col * 128];
                         plane[2 * (rowoff + G)] = (cpart == 0 && G == Gr ? 1.0 : 0.0) - vsp * a.vs[G] * ch;
                         if (a.chi) {
                             double* dst = reinterpret_cast<double*>(a.chi + ((size_t)iw * a.ng + G) * a.ng + Gr);

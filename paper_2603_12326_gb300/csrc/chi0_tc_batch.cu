@@ -63,7 +63,7 @@ struct BArgs {
     const float2* wtab;       // [inst][wld] W_t(w_inst)
     long long wld;
     double pref;
-    double* acc64;            // [grid][128][NMAX]
+    double* acc64;            // [grid][NMAX][128] (column-major: a warp's 32 rows are contiguous)
     double2* eps;
     int* status;
     long long wait_limit;     // clock cycles before a pipeline wait gives up
@@ -261,11 +261,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                 if (((wd + 1) * a.promote) % a.flush == 0 || wd + 1 == nwin) {
                     // the first flush of a tile starts the FP64 sums
                     const bool flushed = wd >= a.flush / a.promote;
-                    double* acc64 = a.acc64 + ((size_t)blockIdx.x * 128 + row) * NMAX + hc * nch8 * 8;
+                    double* acc64 = a.acc64 + (size_t)blockIdx.x * 128 * NMAX + (size_t)(hc * nch8 * 8) * 128 + row;
 #pragma unroll
                     for (int c = 0; c < MAXHALF; ++c) {
                         if (c < nch8 * 8) {
-                            acc64[c] = (flushed ? acc64[c] : 0.0) + (double)part[c];
+                            acc64[(size_t)c * 128] = (flushed ? acc64[(size_t)c * 128] : 0.0) + (double)part[c];
                             part[c] = 0.0f;
                         }
                     }
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
             const int gb = tl.y, n0 = tl.z, half = (tl.w & 0xFFFF) >> 1, ng = a.inst[tl.x].ng;
             const int cpart = row >> 6, gro = row & 63;
             const int Gr = gb * GBLK + gro;
-            const double* acc64 = a.acc64 + ((size_t)blockIdx.x * 128 + row) * NMAX + hc * half;
+            const double* acc64 = a.acc64 + (size_t)blockIdx.x * 128 * NMAX + (size_t)(hc * half) * 128 + row;
             if (Gr < ng) {
                 const double* vs = a.inst[tl.x].vs;
                 const double vsp = vs[Gr];
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc_batch(const __grid_cons
                 for (int col = 0; col < half; ++col) {
                     const int G = n0 + hc * half + col;
                     if (G < ng) {
-                        const double ch = a.pref * acc64[col];
+                        const double ch = a.pref * acc64[(size_t)col * 128];
                         plane[2 * G] = (cpart == 0 && G == Gr ? 1.0 : 0.0) - vsp * vs[G] * ch;
                     }
                 }

@@ -18,8 +18,8 @@ and that when the producer leaves no copy is in flight and when TMEM is freed
 no MMA is.  The same model runs with waits that give up (a wait limit that
 runs out, or copies withheld so that nothing completes): the abort must still
 end every role with its copies landed and its MMAs finished.  Ring depth and
-window length are read from the kernel sources (four stages, windows of two
-for both kernels).  The copy and A-tile barriers are indexed by the stage
+window length are read from the kernel sources (four stages; windows of four
+in the per-q kernel, two in the batch kernel).  The copy and A-tile barriers are indexed by the stage
 modulo (number of A groups, at least two) x ring depth, so a barrier's
 previous phase always belongs to the same A-warp group and lies two windows
 back for an issuer.  A ring shorter than the window, where an issuer's wait
@@ -250,7 +250,7 @@ def test_model_matches_the_kernel_sources():
     # the per-q kernel: eight A warps (warps 4-11) and eight drain warps (12-19)
     assert _constant("AGEN_WARP0", "chi0_tc.cu") == 4 and _constant("DRAIN_WARP0", "chi0_tc.cu") == 12
     assert _constant("NTHREADS", "chi0_tc.cu") == 640
-    assert _constant("PROMOTE", "chi0_tc.cu") == 2
+    assert _constant("PROMOTE", "chi0_tc.cu") == 4
     assert "a.promote = 2;" in _src("chi0_tc_batch.cu")
     assert "for (int it = max(0, last - NSTAGE + 1); it <= last; ++it)" in _src("chi0_tc.cu")
 
