@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one k_chi0_tc launch over 1 q x 200 w of the mid workload, from one ncu capture
 # of `bench.py --profile-case mid200` (dram__bytes_read.sum + dram__bytes_write.sum), and the commit of the kernel
 # source it was taken at; None once the kernel has changed since.
-CHI0_TRAFFIC = None
+CHI0_TRAFFIC = {"bytes": 719424512 + 181569536, "commit": "dc4c689"}
 # Executed FP32 flops of one k_pair_density_fused launch over 1 q of the mid workload (512 k x 181 G), from the
 # ncu thread-instruction counters of `bench.py --profile-case mid` (2 FFMA + FADD + FMUL,
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), and the commit of the kernel source.
