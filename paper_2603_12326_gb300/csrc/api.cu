@@ -233,8 +233,9 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
         return ctx->fail(QCX_ERR_ARG, "set_states: bad arguments");
     if ((long long)nk * nv * nc > (1ll << 30)) return ctx->fail(QCX_ERR_ARG, "set_states: too many transitions");
     cudaSetDevice(ctx->device);
-    std::vector<double> qh;
+    std::vector<double> qh, kh;
     CUDA_OR_FAIL(fetch(ctx, qh, qpts, 3 * (size_t)nq), "set_states qpts");
+    CUDA_OR_FAIL(fetch(ctx, kh, kpts, 3 * (size_t)nk), "set_states kpts");
     if (!finite_all(qh.data(), qh.size())) return ctx->fail(QCX_ERR_ARG, "set_states: non-finite q");
     const size_t nb = ctx->nb;
     const size_t nCk = (size_t)nk * nb * nv, nCkq = (size_t)nq * nk * nb * nc;
@@ -256,6 +257,7 @@ qcx_status qcx_set_states(qcx_ctx* ctx, int nk, const double* kpts, int nv, cons
     k_to_float2<<<nblocks(nCkq), 256, 0, ctx->stream>>>(ctx->d_Ckq64.as<double2>(), ctx->d_Ckq32.as<float2>(), nCkq);
     CUDA_OR_FAIL(cudaGetLastError(), "convert states");
     ++ctx->gen;
+    ctx->kpts_h = kh;
     ctx->nk = nk;
     ctx->nv = nv;
     ctx->nc = nc;
@@ -294,6 +296,11 @@ qcx_status qcx_pair_density(qcx_ctx* ctx, int iq, int ng, const int* G_int, qcx_
     CUDA_OR_FAIL(ctx->scratch2.ensure(3 * sizeof(int) * ng), "alloc");
     CUDA_OR_FAIL(qcx_copy_in(ctx, ctx->scratch2.p, G_int, 3 * sizeof(int) * ng), "copy G");
     CUDA_OR_FAIL(qcx_launch_qsetup(ctx, s, ctx->scratch2.as<int>(), ng, &ctx->qpts[3 * iq]), "q setup");
+    if (prec == QCX_MIXED) {
+        std::vector<int> Gh;
+        CUDA_OR_FAIL(fetch(ctx, Gh, G_int, 3 * (size_t)ng), "G list");
+        CUDA_OR_FAIL(qcx_pd_tab_prepare(ctx, s, Gh.data(), ng, iq), "pair-density tables");
+    }
     if (prec == QCX_FP64) {
         CUDA_OR_FAIL(s.rho.ensure((size_t)ng * nt * sizeof(double2)), "alloc rho");
     } else {

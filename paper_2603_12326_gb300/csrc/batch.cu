@@ -459,6 +459,11 @@ qcx_status build_plan(qcx_ctx* ctx, BatchPlan& p) {
     CUDA_OR_FAIL(cudaMemcpyAsync(p.d_G.p, Gflat.data(), sizeof(int) * Gflat.size(), cudaMemcpyHostToDevice,
                                  ctx->stream),
                  "copy G");
+    if (mixed)   // tables of the FP32 pair densities per slot, planned before the graph is captured
+        for (int s = 0; s < p.nslot; ++s)
+            CUDA_OR_FAIL(qcx_pd_tab_prepare(ctx, *p.qs[s], Gflat.data() + 3 * p.slot_gofs[s], p.slot_u[s],
+                                            p.slot_iq[s]),
+                         "pair-density tables");
     CUDA_OR_FAIL(p.d_inst.ensure(sizeof(BatchInst) * ninst), "alloc");
     CUDA_OR_FAIL(p.d_eps.ensure(sizeof(double2) * eps_off), "alloc eps");
     CUDA_OR_FAIL(p.d_work.ensure((mixed ? sizeof(float2) : sizeof(double2)) * work_off), "alloc work");

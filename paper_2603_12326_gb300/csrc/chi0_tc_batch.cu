@@ -9,7 +9,7 @@
 // densities) and A = W rho~ in three BF16 terms, the five products
 // a0 b0 + a0 b1 + a1 b0 + a1 b1 + a2 b0 (both sides carry the same rho~, so only
 // A's split and the dropped a2 b1 are errors of the contraction),
-// FP32 accumulation restarted after 40 MMAs (four K stages) and promoted
+// FP32 accumulation restarted after 20 MMAs (two K stages) and promoted
 // through FP32 registers into an FP64 buffer, and eps = delta - v^1/2 chi0 v^1/2
 // written in FP64 (row G', column G).
 //
@@ -67,7 +67,7 @@ struct BArgs {
     double2* eps;
     int* status;
     long long wait_limit;     // clock cycles before a pipeline wait gives up
-    int promote;              // K stages per accumulation window (40 MMAs)
+    int promote;              // K stages per accumulation window (20 MMAs)
     int flush;                // K stages between FP64 flushes (64 windows)
 };
 
@@ -387,7 +387,7 @@ cudaError_t qcx_launch_chi0_tc_batch(cudaStream_t st, const CUtensorMap* maps, i
     a.eps = eps;
     a.status = status;
     a.wait_limit = wait_limit;
-    a.promote = 4;                            // 40 MMAs per window: four K stages of ten
+    a.promote = 2;                            // 20 MMAs per window: two K stages of ten
     a.flush = 64 * a.promote;
     cudaError_t e =
         cudaFuncSetAttribute((const void*)k_chi0_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);

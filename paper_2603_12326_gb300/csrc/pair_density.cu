@@ -55,6 +55,14 @@ template <typename T> struct PDArgs {
     __nv_bfloat162* R2;      // x2 = bf16(x - x0 - x1)
     long long kp2;           // row length of the BF16 planes in bf16x2 units
     cplx<T>* Sout;           // overlap mode: [nk][nb][nb]
+    // tables of the mixed path (PdTab): one-dimensional factors per (pair, axis, k class, q+G
+    // class) and the factor of (pair, G)
+    const float2* ptab;      // [entries][NCH][4]
+    const float2* pcmn;      // [npair][ng]
+    const int* kidx;         // [nk][3]
+    const int* gidx;         // [ng][3]
+    int nkx[3], nqx[3];
+    long long tbase[4];
 };
 
 // z^n for integer n (|n| small) by repeated squaring
@@ -72,6 +80,11 @@ template <typename C> __device__ __forceinline__ C cpow_int(C z, int n) {
     if (n < 0) r.y = -r.y;     // |z| = 1: z^-n = conj(z^n)
     return r;
 }
+
+template <typename T, int NCH>
+__device__ __forceinline__ void assemble_block(const PDArgs<T>& a, int ga, int gb, T p, T ap, T bp,
+                                               const cplx<T>& common, const cplx<T> (&E)[3][NCH][4],
+                                               cplx<T> (&out)[4][4]);
 
 // One group pair's 4 x 4 block of B (components s, p_x, p_y, p_z of each group;
 // absent components are left unset).
@@ -121,6 +134,17 @@ __device__ __forceinline__ void pair_block_vals(const PDArgs<T>& a, int ip, cons
                                cscale(M0, inv2p - tk * tk));                  // E(1,1)
         }
     }
+    assemble_block<T, NCH>(a, ga, gb, p, ap, bp, common, E, out);
+}
+
+// The 4 x 4 block from the one-dimensional factors of the three axes: component (ca, cb) takes
+// per axis the factor of its Cartesian powers, summed over the characters, times the common factor
+// and the p normalisations.
+template <typename T, int NCH>
+__device__ __forceinline__ void assemble_block(const PDArgs<T>& a, int ga, int gb, T p, T ap, T bp,
+                                               const cplx<T>& common, const cplx<T> (&E)[3][NCH][4],
+                                               cplx<T> (&out)[4][4]) {
+    using C = cplx<T>;
     // components: 0 = s, 1..3 = p_x, p_y, p_z
     const int ma = a.grp_mask[ga], mb = a.grp_mask[gb];
     const T fa = T(2) * sqrt(ap * p), fb = T(2) * sqrt(bp * p);   // p normalisation 2 sqrt(alpha)
@@ -182,6 +206,112 @@ __device__ __forceinline__ void store_split3(float re, float im, __nv_bfloat162*
     R2[o] = __floats2bfloat162_rn(rr - mf.x, ri - mf.y);
 }
 
+// Arguments of the table kernels (arithmetic in T, FP32 results).
+template <typename T> struct PdTabArgs {
+    const T* par;            // [npair][8]
+    const cplx<T>* tab;      // lattice terms {w_n, d_n}
+    const int* dir_off;
+    const int* dir_cnt;
+    const int* dir_nlo;
+    T h;
+    T charre[4][3], charim[4][3];
+    const double* kval;      // k classes, axes concatenated
+    const double* qval;      // q+G classes, axes concatenated
+    const T* kappa;          // [ng][3] q + G
+    int nkx[3], nqx[3], kofs[3], qofs[3];
+    long long tbase[4];
+    int npair, ng;
+    float2* out;             // [entries][NCH][4]
+    float2* cmn;             // [npair][ng]
+};
+
+// One entry of the one-dimensional table: for shell-group pair ip, axis x, the k component of
+// class ik and the q+G component of class iq, the factors E(0,0), E(1,0), E(0,1), E(1,1) of every
+// character, by the lattice sum of pair_block_vals (same operations, same order) in T.
+template <typename T, int NCH> __global__ void k_pd_axis_table(PdTabArgs<T> a) {
+    using C = cplx<T>;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= a.tbase[3]) return;
+    const int x = e < a.tbase[1] ? 0 : (e < a.tbase[2] ? 1 : 2);
+    long long r = e - a.tbase[x];
+    const int iq = (int)(r % a.nqx[x]);
+    r /= a.nqx[x];
+    const int ik = (int)(r % a.nkx[x]);
+    const int ip = (int)(r / a.nkx[x]);
+    const T kk = (T)a.kval[a.kofs[x] + ik], kap = (T)a.qval[a.qofs[x] + iq];
+    const T* par = a.par + (size_t)ip * 8;
+    const T p = par[0], ap = par[1], bp = par[2];
+    const T inv2p = T(0.5) / p;
+    const int di = ip * 3 + x;
+    const int off = a.dir_off[di], cnt = a.dir_cnt[di], nlo = a.dir_nlo[di];
+    const T theta = (kk + bp * kap) * a.h;
+    const T tk = kap * inv2p;
+    T zs, zc;
+    sincos_t(theta, &zs, &zc);
+    const C z = mk<T>(zc, zs);
+    float4* out = reinterpret_cast<float4*>(a.out + e * (NCH * 4));
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        const C zch = ch ? cmul(z, mk<T>(a.charre[ch][x], a.charim[ch][x])) : z;
+        C zn = cpow_int(zch, nlo);
+        C M0 = mk<T>(0, 0), M1 = mk<T>(0, 0), M2 = mk<T>(0, 0);
+        for (int j = 0; j < cnt; ++j) {
+            const C wd = a.tab[off + j];
+            const C t0 = cscale(zn, wd.x);
+            M0 = cadd(M0, t0);
+            const C t1 = cscale(t0, wd.y);
+            M1 = cadd(M1, t1);
+            M2 = cadd(M2, cscale(t1, wd.y));
+            zn = cmul(zn, zch);
+        }
+        const C itkM0 = mk<T>(-tk * M0.y, tk * M0.x);
+        const C itkM1 = mk<T>(-tk * M1.y, tk * M1.x);
+        const C e10 = cadd(cscale(M1, -bp), itkM0);
+        const C e01 = cadd(cscale(M1, ap), itkM0);
+        const C e11 = cadd(cadd(cscale(M2, -ap * bp), cscale(itkM1, ap - bp)), cscale(M0, inv2p - tk * tk));
+        out[2 * ch] = make_float4((float)M0.x, (float)M0.y, (float)e10.x, (float)e10.y);
+        out[2 * ch + 1] = make_float4((float)e01.x, (float)e01.y, (float)e11.x, (float)e11.y);
+    }
+}
+
+// The factor of pair ip and G: pref e^{-|q+G|^2/4p} e^{i (q+G).P} / (number of characters), in T.
+template <typename T, int NCH> __global__ void k_pd_common(PdTabArgs<T> a) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)a.npair * a.ng) return;
+    const int ip = (int)(i / a.ng), g = (int)(i - (long long)ip * a.ng);
+    const T* par = a.par + (size_t)ip * 8;
+    const T kap[3] = {a.kappa[3 * g], a.kappa[3 * g + 1], a.kappa[3 * g + 2]};
+    const T k2 = kap[0] * kap[0] + kap[1] * kap[1] + kap[2] * kap[2];
+    T s, c;
+    sincos_t(kap[0] * par[4] + kap[1] * par[5] + kap[2] * par[6], &s, &c);
+    const T amp = par[3] * exp_t(-k2 * T(0.25) / par[0]) / T(NCH);
+    a.cmn[i] = make_float2((float)(amp * c), (float)(amp * s));
+}
+
+// One group pair's block from the tables (k classes kx, q+G classes gx of this thread's G).
+template <int NCH>
+__device__ __forceinline__ void pair_block_tab(const PDArgs<float>& a, int ip, int ga, int gb, const int (&kx)[3],
+                                               const int (&gx)[3], int g, cplx<float> (&out)[4][4]) {
+    using C = cplx<float>;
+    const float* par = a.par + (size_t)ip * 8;
+    const float2 cm = a.pcmn[(size_t)ip * a.ng + g];
+    C E[3][NCH][4];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const float4* src = reinterpret_cast<const float4*>(
+            a.ptab + (a.tbase[x] + ((long long)ip * a.nkx[x] + kx[x]) * a.nqx[x] + gx[x]) * (NCH * 4));
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            const float4 u = src[2 * ch], v = src[2 * ch + 1];
+            E[x][ch][0] = mk<float>(u.x, u.y);
+            E[x][ch][1] = mk<float>(u.z, u.w);
+            E[x][ch][2] = mk<float>(v.x, v.y);
+            E[x][ch][3] = mk<float>(v.z, v.w);
+        }
+    }
+    assemble_block<float, NCH>(a, ga, gb, par[0], par[1], par[2], mk<float>(cm.x, cm.y), E, out);
+}
+
 template <typename T, int NCH>
 __global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
     using C = cplx<T>;
@@ -238,10 +368,14 @@ __global__ void __launch_bounds__(PD_THREADS) k_pair_density(PDArgs<T> a) {
 // memory.  Threads are ordered G fastest, so a warp holds one or two groups a
 // and every thread of it runs the same pair's lattice sums.  Y then goes to
 // shared memory and rho = C_kq^H Y is formed per (G, v, c).  The sums run in
-// the same order as in k_pair_density.
+// the same order as in k_pair_density.  With the tables of PdTab (TAB) the
+// one-dimensional lattice sums and the (pair, G) factor are read, not formed
+// per (k, G).
 template <int NV> constexpr int pdf_maxt() { return NV <= 4 ? PDF_MAXT : (NV <= 8 ? 256 : 192); }
 
-template <int NCH, int NV>
+// TAB: the one-dimensional factors and the common factor come from the tables of this q (PdTab)
+// instead of being formed per (k, G).
+template <int NCH, int NV, bool TAB>
 __global__ void __launch_bounds__(pdf_maxt<NV>()) k_pair_density_fused(PDArgs<float> a) {
     using C = cplx<float>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,6 +396,14 @@ __global__ void __launch_bounds__(pdf_maxt<NV>()) k_pair_density_fused(PDArgs<fl
         const int g = g0 + gl;
         const float kap[3] = {a.kappa[3 * g], a.kappa[3 * g + 1], a.kappa[3 * g + 2]};
         const float k2 = kap[0] * kap[0] + kap[1] * kap[1] + kap[2] * kap[2];
+        int kx[3] = {0, 0, 0}, gx[3] = {0, 0, 0};
+        if (TAB) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                kx[x] = a.kidx[3 * k + x];
+                gx[x] = a.gidx[3 * g + x];
+            }
+        }
         C Y[4][NV];
 #pragma unroll
         for (int ca = 0; ca < 4; ++ca)
@@ -269,7 +411,10 @@ __global__ void __launch_bounds__(pdf_maxt<NV>()) k_pair_density_fused(PDArgs<fl
             for (int v = 0; v < NV; ++v) Y[ca][v] = mk<float>(0, 0);
         for (int gb = 0; gb < a.ngrp; ++gb) {
             C blk[4][4];
-            pair_block_vals<float, NCH>(a, ga * a.ngrp + gb, kk, kap, k2, blk);
+            if (TAB)
+                pair_block_tab<NCH>(a, ga * a.ngrp + gb, ga, gb, kx, gx, g, blk);
+            else
+                pair_block_vals<float, NCH>(a, ga * a.ngrp + gb, kk, kap, k2, blk);
             const int mb = a.grp_mask[gb];
             const int nu0 = a.grp_mu0[gb] - ((mb & 1) ? 0 : 1);
 #pragma unroll
@@ -414,9 +559,14 @@ template <typename T, int NCH> cudaError_t launch_pd(qcx_ctx* ctx, PDArgs<T>& a,
 }
 
 template <int NCH, int NV> cudaError_t launch_fused(qcx_ctx* ctx, PDArgs<float>& a, size_t smem, dim3 grid, int nthr) {
-    cudaError_t e = set_smem<float>((const void*)k_pair_density_fused<NCH, NV>, smem);
-    if (e != cudaSuccess) return e;
-    k_pair_density_fused<NCH, NV><<<grid, nthr, smem, ctx->stream>>>(a);
+    cudaError_t e;
+    if (a.ptab) {
+        if ((e = set_smem<float>((const void*)k_pair_density_fused<NCH, NV, true>, smem)) != cudaSuccess) return e;
+        k_pair_density_fused<NCH, NV, true><<<grid, nthr, smem, ctx->stream>>>(a);
+        return cudaGetLastError();
+    }
+    if ((e = set_smem<float>((const void*)k_pair_density_fused<NCH, NV, false>, smem)) != cudaSuccess) return e;
+    k_pair_density_fused<NCH, NV, false><<<grid, nthr, smem, ctx->stream>>>(a);
     return cudaGetLastError();
 }
 template <int NCH> cudaError_t launch_fused_nv(qcx_ctx* ctx, PDArgs<float>& a, size_t smem, dim3 grid, int nthr) {
@@ -597,6 +747,81 @@ cudaError_t qcx_launch_qsetup(qcx_ctx* ctx, QSlot& s, const int* d_G, int ng, co
     return cudaGetLastError();
 }
 
+// Classes of the components v[3 i + x] of n points along axis x: values equal to a class's first
+// value within 1e-9 (relative) share it; idx[3 i + x] receives the class, vals the float values.
+static void axis_classes(const double* v, int n, int x, std::vector<double>& vals, std::vector<int>& idx) {
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int i, int j) { return v[3 * i + x] < v[3 * j + x]; });
+    int cls = -1;
+    double first = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double d = v[3 * ord[j] + x];
+        if (cls < 0 || fabs(d - first) > 1e-9 * fmax(1.0, fabs(d))) {
+            ++cls;
+            first = d;
+            vals.push_back(d);
+        }
+        idx[3 * ord[j] + x] = cls;
+    }
+}
+
+cudaError_t qcx_pd_tab_prepare(qcx_ctx* ctx, QSlot& s, const int* G_host, int ng, int iq) {
+    PdTab& t = s.pdt;
+    t.valid = false;
+    const int nk = ctx->nk, npair = ctx->ngrp * ctx->ngrp;
+    if ((int)ctx->kpts_h.size() != 3 * nk || npair < 1) return cudaSuccess;
+    // q + G in Cartesian components (reciprocal basis b_i = 2 pi inv(A)^T rows)
+    const double* A = ctx->lattice;
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    const double inv[9] = {(A[4] * A[8] - A[5] * A[7]) / det, (A[2] * A[7] - A[1] * A[8]) / det,
+                           (A[1] * A[5] - A[2] * A[4]) / det, (A[5] * A[6] - A[3] * A[8]) / det,
+                           (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
+                           (A[3] * A[7] - A[4] * A[6]) / det, (A[1] * A[6] - A[0] * A[7]) / det,
+                           (A[0] * A[4] - A[1] * A[3]) / det};
+    const double* q = &ctx->qpts[3 * iq];
+    std::vector<double> kap(3 * (size_t)ng);
+    for (int g = 0; g < ng; ++g)
+        for (int x = 0; x < 3; ++x) {
+            double v = q[x];
+            for (int i = 0; i < 3; ++i) v += G_host[3 * g + i] * 2.0 * M_PI * inv[3 * x + i];
+            kap[3 * g + x] = v;
+        }
+    std::vector<double> kval, qval;
+    std::vector<int> kidx(3 * (size_t)nk), gidx(3 * (size_t)ng);
+    long long cells = 0;
+    for (int x = 0; x < 3; ++x) {
+        t.kofs[x] = (int)kval.size();
+        t.qofs[x] = (int)qval.size();
+        axis_classes(ctx->kpts_h.data(), nk, x, kval, kidx);
+        axis_classes(kap.data(), ng, x, qval, gidx);
+        t.nkx[x] = (int)kval.size() - t.kofs[x];
+        t.nqx[x] = (int)qval.size() - t.qofs[x];
+        cells += (long long)t.nkx[x] * t.nqx[x];
+    }
+    // worth it only when the classes repeat (regular k grids, G shells); bounded memory
+    const int nch = ctx->nchar;
+    const size_t tab_bytes = (size_t)npair * cells * nch * 4 * sizeof(float2);
+    if (4 * cells > 3LL * 3 * nk * ng || tab_bytes > ((size_t)512 << 20)) return cudaSuccess;
+    for (int x = 0; x < 3; ++x) t.tbase[x + 1] = t.tbase[x] + (long long)npair * t.nkx[x] * t.nqx[x];
+    cudaError_t e;
+    if ((e = t.tab.ensure(tab_bytes)) != cudaSuccess) return e;
+    if ((e = t.cmn.ensure((size_t)npair * ng * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = t.kidx.ensure(kidx.size() * sizeof(int))) != cudaSuccess) return e;
+    if ((e = t.gidx.ensure(gidx.size() * sizeof(int))) != cudaSuccess) return e;
+    if ((e = t.kval.ensure(kval.size() * sizeof(double))) != cudaSuccess) return e;
+    if ((e = t.qval.ensure(qval.size() * sizeof(double))) != cudaSuccess) return e;
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+    if ((e = cudaMemcpyAsync(t.kidx.p, kidx.data(), kidx.size() * sizeof(int), h2d, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(t.gidx.p, gidx.data(), gidx.size() * sizeof(int), h2d, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(t.kval.p, kval.data(), kval.size() * sizeof(double), h2d, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(t.qval.p, qval.data(), qval.size() * sizeof(double), h2d, ctx->stream)) != cudaSuccess)
+        return e;
+    t.valid = true;
+    return cudaSuccess;
+}
+
 cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precision prec) {
     const int nt = ctx->nk * ctx->nv * ctx->nc;
     const int gpc = 8;
@@ -659,6 +884,64 @@ cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precisio
     a.R1 = a.R0 + (size_t)s.ngp * (s.kp / 2);
     a.R2 = a.R1 + (size_t)s.ngp * (s.kp / 2);
     a.kp2 = s.kp / 2;
+    if (gcf && s.pdt.valid) {
+        // tables of this q first (FP32, the operations of pair_block_vals: FP64 tables were no more
+        // accurate in the loss and cost ~2 ms per mid q at the GB300's FP64 rate): the one-dimensional
+        // factors, then the factor of (pair, G)
+        const PdTab& t = s.pdt;
+        PdTabArgs<float> ta{};
+        ta.par = ctx->pairs.par32.as<float>();
+        ta.tab = ctx->pairs.tab32.as<float2>();
+        ta.dir_off = ctx->pairs.dir_off.as<int>();
+        ta.dir_cnt = ctx->pairs.dir_cnt.as<int>();
+        ta.dir_nlo = ctx->pairs.dir_nlo.as<int>();
+        ta.h = (float)ctx->h;
+        for (int c = 0; c < 4; ++c)
+            for (int x = 0; x < 3; ++x) {
+                ta.charre[c][x] = (float)cos(2.0 * M_PI * ctx->chars[c][x]);
+                ta.charim[c][x] = (float)sin(2.0 * M_PI * ctx->chars[c][x]);
+            }
+        ta.kval = t.kval.as<double>();
+        ta.qval = t.qval.as<double>();
+        ta.kappa = s.kappa32.as<float>();
+        for (int x = 0; x < 3; ++x) {
+            ta.nkx[x] = t.nkx[x];
+            ta.nqx[x] = t.nqx[x];
+            ta.kofs[x] = t.kofs[x];
+            ta.qofs[x] = t.qofs[x];
+        }
+        for (int x = 0; x < 4; ++x) ta.tbase[x] = t.tbase[x];
+        ta.npair = ctx->ngrp * ctx->ngrp;
+        ta.ng = s.ng;
+        ta.out = t.tab.as<float2>();
+        ta.cmn = t.cmn.as<float2>();
+        const unsigned gt = (unsigned)((t.tbase[3] + 255) / 256);
+        const unsigned gcm = (unsigned)(((long long)ta.npair * s.ng + 255) / 256);
+        switch (ctx->nchar) {
+            case 1:
+                k_pd_axis_table<float, 1><<<gt, 256, 0, ctx->stream>>>(ta);
+                k_pd_common<float, 1><<<gcm, 256, 0, ctx->stream>>>(ta);
+                break;
+            case 2:
+                k_pd_axis_table<float, 2><<<gt, 256, 0, ctx->stream>>>(ta);
+                k_pd_common<float, 2><<<gcm, 256, 0, ctx->stream>>>(ta);
+                break;
+            default:
+                k_pd_axis_table<float, 4><<<gt, 256, 0, ctx->stream>>>(ta);
+                k_pd_common<float, 4><<<gcm, 256, 0, ctx->stream>>>(ta);
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        a.ptab = t.tab.as<float2>();
+        a.pcmn = t.cmn.as<float2>();
+        a.kidx = t.kidx.as<int>();
+        a.gidx = t.gidx.as<int>();
+        for (int x = 0; x < 3; ++x) {
+            a.nkx[x] = t.nkx[x];
+            a.nqx[x] = t.nqx[x];
+        }
+        for (int x = 0; x < 4; ++x) a.tbase[x] = t.tbase[x];
+    }
     if (gcf) {
         a.g_per_cta = gcf;
         const dim3 gridf(ctx->nk, (s.ng + gcf - 1) / gcf);

@@ -36,6 +36,20 @@ struct DevBuf {
     template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Tables of the FP32 pair densities for one q: the one-dimensional lattice sums per shell-group
+// pair, axis, distinct k component and distinct (q+G) component, and the factor that depends on
+// the pair and G only, so the per-(k, G) kernel reads them instead of forming them again.
+struct PdTab {
+    bool valid = false;
+    int nkx[3] = {0, 0, 0}, nqx[3] = {0, 0, 0};   // distinct k and q+G components per axis
+    int kofs[3] = {0, 0, 0}, qofs[3] = {0, 0, 0}; // first value of each axis in kval / qval
+    long long tbase[4] = {0, 0, 0, 0};            // first entry of each axis (tbase[3] = entries)
+    DevBuf kidx, gidx;         // [nk][3], [ng][3] int: class of each point's component
+    DevBuf kval, qval;         // float values of the classes (axes concatenated)
+    DevBuf tab;                // [entries][nchar][4] float2: E(0,0), E(1,0), E(0,1), E(1,1)
+    DevBuf cmn;                // [npair][ng] float2
+};
+
 // Per-precision working set of one q.
 struct QSlot {
     int iq = -1;               // q whose pair densities are stored here
@@ -61,6 +75,7 @@ struct QSlot {
     int ngp = 0;               // padded G rows of the BF16 planes (multiple of 16)
     long long kp = 0;          // padded K' = 2 nt columns of the BF16 planes
     double eta = 0.0;
+    PdTab pdt;                 // MIXED: tables of the pair-density kernel for this slot's q and G list
 };
 
 // Loss tables kept per q after qcx_invert_eps.
@@ -179,6 +194,7 @@ struct qcx_ctx {
     // states
     int nk = 0, nv = 0, nc = 0, nq = 0;
     std::vector<double> qpts;  // host copy
+    std::vector<double> kpts_h;    // host copy [nk][3]
     DevBuf d_kpts, d_kpts32;   // [nk][3]
     DevBuf d_Ck64, d_Ck32;     // [nk][nb][nv]
     DevBuf d_Ek;               // [nk][nv]
@@ -247,6 +263,10 @@ cudaError_t qcx_copy_out(qcx_ctx* ctx, void* dst, const void* src_dev, size_t by
 // pair densities (pair_density.cu)
 cudaError_t qcx_launch_qsetup(qcx_ctx* ctx, QSlot& s, const int* d_G, int ng, const double* q);
 cudaError_t qcx_launch_pair_density(qcx_ctx* ctx, QSlot& s, int iq, qcx_precision prec);
+// Plan and upload the tables of the FP32 pair densities for q number iq and the host G list (outside
+// any stream capture); leaves s.pdt invalid (the kernel then forms every term itself) when the
+// tables would not save work or exceed their memory budget.
+cudaError_t qcx_pd_tab_prepare(qcx_ctx* ctx, QSlot& s, const int* G_host, int ng, int iq);
 cudaError_t qcx_launch_overlap(qcx_ctx* ctx, int nk, const double* d_kpts, double2* d_out);
 cudaError_t qcx_pair_density_configure();
 

@@ -18,7 +18,7 @@ and that when the producer leaves no copy is in flight and when TMEM is freed
 no MMA is.  The same model runs with waits that give up (a wait limit that
 runs out, or copies withheld so that nothing completes): the abort must still
 end every role with its copies landed and its MMAs finished.  Ring depth and
-window length are read from the kernel sources (four stages, windows of four
+window length are read from the kernel sources (four stages, windows of two
 for both kernels).  The copy and A-tile barriers are indexed by the stage
 modulo (number of A groups, at least two) x ring depth, so a barrier's
 previous phase always belongs to the same A-warp group and lies two windows
@@ -250,8 +250,8 @@ def test_model_matches_the_kernel_sources():
     # the per-q kernel: eight A warps (warps 4-11) and eight drain warps (12-19)
     assert _constant("AGEN_WARP0", "chi0_tc.cu") == 4 and _constant("DRAIN_WARP0", "chi0_tc.cu") == 12
     assert _constant("NTHREADS", "chi0_tc.cu") == 640
-    assert _constant("PROMOTE", "chi0_tc.cu") == 4
-    assert "a.promote = 4;" in _src("chi0_tc_batch.cu")
+    assert _constant("PROMOTE", "chi0_tc.cu") == 2
+    assert "a.promote = 2;" in _src("chi0_tc_batch.cu")
     assert "for (int it = max(0, last - NSTAGE + 1); it <= last; ++it)" in _src("chi0_tc.cu")
 
 
@@ -287,10 +287,10 @@ def test_batch_kernel_protocol_across_tiles(kstages, ntile):
     the stage and window counters continuing across tiles."""
     nstage = _constant("NSTAGE", "chi0_tc_batch.cu")
     for seed in range(10):
-        errors, aborted = _run(kstages, nstage, 4, seed, ngroups=1, ntile=ntile)
+        errors, aborted = _run(kstages, nstage, 2, seed, ngroups=1, ntile=ntile)
         assert not errors and not aborted, (kstages, ntile, seed, errors[:3])
     for seed in range(10):
-        errors, aborted = _run(kstages, nstage, 4, seed, ngroups=1, ntile=ntile, timeouts=True)
+        errors, aborted = _run(kstages, nstage, 2, seed, ngroups=1, ntile=ntile, timeouts=True)
         assert not errors, (kstages, ntile, seed, errors[:3])
 
 
