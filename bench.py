@@ -34,11 +34,11 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one k_chi0_tc launch over 1 q x 200 w of the mid workload, from one ncu capture
 # of `bench.py --profile-case mid200` (dram__bytes_read.sum + dram__bytes_write.sum), and the commit of the kernel
 # source it was taken at; None once the kernel has changed since.
-CHI0_TRAFFIC = {"bytes": 719424512 + 181569536, "commit": "dc4c689"}
+CHI0_TRAFFIC = {"bytes": 719207680 + 182851072, "commit": "1fa000c"}
 # Executed FP32 flops of one k_pair_density_fused launch over 1 q of the mid workload (512 k x 181 G), from the
 # ncu thread-instruction counters of `bench.py --profile-case mid` (2 FFMA + FADD + FMUL,
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), and the commit of the kernel source.
-PD_FP32_FLOPS = None   # not recounted since the kernel reads its lattice sums from per-q tables
+PD_FP32_FLOPS = {"flops": 2 * 26974224384 + 3570466816 + 10942709760, "commit": "1fa000c"}
 METRIC = "eps^-1 (q,w) blocks/s vs FP64 plain GPU path at <=1e-4 rel err; tensor-pipe %"
 WORKLOAD = ("mid: diamond a=5.43 A, 12 sp shells/atom (N_b=96), 8x8x8 k, N_v=4, N_c=32 (N_t=65536), "
             "N_G=181, 50 q x 200 w on 0-60 eV, eta=0.1 eV")
