@@ -440,13 +440,15 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
  * paper), written to out[0 .. n-1] (host):
  * [0] tile width cap (columns of G per tensor-core tile), [1] tiles,
  * [2] persistent tensor-core CTAs, [3] solve CTAs, [4] kernels per replay,
- * [5] 1 if the tile width was autotuned, [6] distinct q, [7] largest N_G,
- * [8] autotuning time (microseconds), [9] precision.  Entries past 9 are 0.
+ * [5] 1 if the tile widths were autotuned, [6] distinct q, [7] largest N_G,
+ * [8] autotuning time (microseconds), [9] precision, [10..12] the tile width
+ * caps of the N_G classes 65-128, 129-192 and above 192 ([0] repeats the last).
+ * Entries past 12 are 0.
  * Errors: QCX_ERR_ARG, QCX_ERR_STATE (no plan yet; out is zeroed). */
 qcx_status qcx_batch_info(const qcx_ctx* ctx, int n, long long* out);
 
 /* Turn the tile-width autotuning of new QCX_MIXED batch plans on (default)
- * or off (then the widest tiles are used); no counterpart in the paper.  Errors: QCX_ERR_ARG (ctx NULL). */
+ * or off (then the widest tiles, caps of 192, are used); no counterpart in the paper.  Errors: QCX_ERR_ARG (ctx NULL). */
 qcx_status qcx_batch_autotune(qcx_ctx* ctx, int enable);
 
 /* ----------------------------------------- learned local-field correction */

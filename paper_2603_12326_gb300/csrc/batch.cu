@@ -16,9 +16,12 @@
 //  * the whole sequence (G set-up, pair densities, W table, chi0 + Dyson,
 //    LU, FP64 residual and correction) is captured once in a CUDA graph and
 //    replayed per call; only the frequencies are uploaded per call.
-//  * Autotuner: on a new plan the mixed path captures one graph per tile
-//    width cap (192, 128, 64 columns of G per tile), times two replays of
-//    each with CUDA events and keeps the fastest.
+//  * Autotuner: the tile width (columns of G per tensor-core tile) has its own
+//    cap per N_G class (65-128, 129-192, more than 192); on a new plan the
+//    mixed path starts from caps of 192, then tries the narrower caps of one
+//    class at a time (widest class first, the others at their best so far),
+//    capturing a graph for each set and timing two replays with CUDA events,
+//    and keeps the fastest.
 #include "qcx_internal.h"
 #include "cplx.cuh"
 
@@ -169,6 +172,7 @@ struct BatchPlan {
     std::vector<CUtensorMap> maps;              // [nslot][3]: the three BF16 planes of each slot
     std::vector<int> grp_tile0, grp_ntile;      // tensor-core tiles per group of <= QCX_BATCH_MAXQ slots
     int tc_grid = 0, tile_cap = 0, ntile = 0;
+    int caps[3] = {192, 192, 192};              // tile width cap per N_G class: (64, 128], (128, 192], > 192
     int lu_grid = 0, n_rtask = 0;
     int tuned = 0;
     double tune_ms = 0.0;
@@ -239,14 +243,21 @@ std::vector<GEntry> g_union(const double* A, const double* q, double gmax) {
     return out;
 }
 
-// tensor-core tiles for a tile-width cap, grouped by slot group, largest N first and, within one
-// width, by q (slot), so the tiles that stream the same pair-density planes run side by side and
-// find them in L2
-void make_tc_tiles(const BatchPlan& p, int cap, std::vector<int4>& tiles, std::vector<int>& g0, std::vector<int>& gn) {
+// N_G class of an instance for the tile-width caps: -1 (at most 64, one tile whatever the cap),
+// 0 (65-128), 1 (129-192), 2 (more than 192)
+int ng_class(int ng) { return ng <= 64 ? -1 : (ng <= 128 ? 0 : (ng <= 192 ? 1 : 2)); }
+
+// tensor-core tiles for the tile-width caps of the N_G classes, grouped by slot group, largest N
+// first and, within one width, by q (slot), so the tiles that stream the same pair-density planes
+// run side by side and find them in L2
+void make_tc_tiles(const BatchPlan& p, const int (&caps)[3], std::vector<int4>& tiles, std::vector<int>& g0,
+                   std::vector<int>& gn) {
     const int ngrp = (p.nslot + QCX_BATCH_MAXQ - 1) / QCX_BATCH_MAXQ;
     std::vector<std::vector<int4>> grp(ngrp);
     for (int i = 0; i < p.ninst; ++i) {
         const int ng = p.hinst[i].ng;
+        const int cls = ng_class(ng);
+        const int cap = cls < 0 ? 192 : caps[cls];
         const int chunks = ng <= cap ? 1 : (ng + cap - 1) / cap;
         const int nc = ((ng + chunks - 1) / chunks + 15) / 16 * 16;
         const int ngb = (ng + 63) / 64;
@@ -541,14 +552,15 @@ qcx_status build_plan(qcx_ctx* ctx, BatchPlan& p) {
     return QCX_OK;
 }
 
-// set the tensor-core tiles for one width cap (uploads the list; no launch).  The
-// tile and accumulator buffers are sized once for every cap before the first
-// capture, so no captured graph ever sees them reallocated.
-qcx_status set_tiles(qcx_ctx* ctx, BatchPlan& p, int cap) {
+// set the tensor-core tiles for the caps of the N_G classes (uploads the list; no launch).  The
+// tile and accumulator buffers are sized once for the narrowest caps before the first capture,
+// so no captured graph ever sees them reallocated.
+qcx_status set_tiles(qcx_ctx* ctx, BatchPlan& p, const int (&caps)[3]) {
     std::vector<int4> tiles;
-    make_tc_tiles(p, cap, tiles, p.grp_tile0, p.grp_ntile);
+    make_tc_tiles(p, caps, tiles, p.grp_tile0, p.grp_ntile);
     p.ntile = (int)tiles.size();
-    p.tile_cap = cap;
+    for (int c = 0; c < 3; ++c) p.caps[c] = caps[c];
+    p.tile_cap = caps[2];
     p.tc_grid = std::min(p.ntile, sm_count(ctx->device));
     if (p.d_tiles.bytes < sizeof(int4) * tiles.size() || p.d_acc.bytes < qcx_chi0_tc_batch_acc_bytes(p.tc_grid))
         return ctx->fail(QCX_ERR_STATE, "solve_batch: tile buffers not sized for this cap");
@@ -592,35 +604,40 @@ qcx_status prepare(qcx_ctx* ctx, BatchPlan& p) {
         CUDA_OR_FAIL(capture(ctx, p, &p.exec), "capture batch graph");
         return QCX_OK;
     }
-    const int caps_all[3] = {192, 128, 64};
-    const int ncap = ctx->batch_tune ? 3 : 1;
+    const bool tune = ctx->batch_tune != 0;
     {
+        // the narrowest caps give the most tiles: size the buffers for them once
         size_t most = 0;
         std::vector<int4> tiles;
         std::vector<int> g0, gn;
-        for (int c = 0; c < 3; ++c) {
-            make_tc_tiles(p, caps_all[c], tiles, g0, gn);
-            most = std::max(most, tiles.size());
-        }
+        const int narrow[3] = {64, 64, 64};
+        make_tc_tiles(p, narrow, tiles, g0, gn);
+        most = tiles.size();
         const int grid = (int)std::min<size_t>(most, (size_t)sm_count(ctx->device));
         CUDA_OR_FAIL(p.d_tiles.ensure(sizeof(int4) * most), "alloc tiles");
         CUDA_OR_FAIL(p.d_acc.ensure(qcx_chi0_tc_batch_acc_bytes(grid)), "alloc acc");
     }
-    double best = 1e300;
-    int best_cap = 192;
+    // classes present in this batch
+    bool present[3] = {false, false, false};
+    for (int i = 0; i < p.ninst; ++i) {
+        const int c = ng_class(p.hinst[i].ng);
+        if (c >= 0) present[c] = true;
+    }
     cudaEvent_t t0, t1;
     CUDA_OR_FAIL(cudaEventCreate(&t0), "event");
     CUDA_OR_FAIL(cudaEventCreate(&t1), "event");
     cudaEventRecord(t0, ctx->stream);
-    for (int c = 0; c < ncap; ++c) {
-        qcx_status st = set_tiles(ctx, p, caps_all[c]);
+    // capture and time one set of caps; keeps its graph when it is the fastest so far
+    double best = 1e300;
+    int best_caps[3] = {192, 192, 192};
+    auto trial = [&](const int (&caps)[3]) -> qcx_status {
+        qcx_status st = set_tiles(ctx, p, caps);
         if (st != QCX_OK) return st;
         cudaGraphExec_t ex = nullptr;
         CUDA_OR_FAIL(capture(ctx, p, &ex), "capture batch graph");
-        if (ncap == 1) {
+        if (!tune) {
             p.exec = ex;
-            best_cap = caps_all[c];
-            break;
+            return QCX_OK;
         }
         double ms = 0.0;
         st = time_exec(ctx, ex, &ms);
@@ -630,11 +647,32 @@ qcx_status prepare(qcx_ctx* ctx, BatchPlan& p) {
         }
         if (ms < best) {
             best = ms;
-            best_cap = caps_all[c];
+            for (int c = 0; c < 3; ++c) best_caps[c] = caps[c];
             if (p.exec) cudaGraphExecDestroy(p.exec);
             p.exec = ex;
         } else {
             cudaGraphExecDestroy(ex);
+        }
+        return QCX_OK;
+    };
+    {
+        const int start[3] = {192, 192, 192};
+        qcx_status st = trial(start);
+        if (st != QCX_OK) return st;
+    }
+    if (tune) {
+        // one pass of coordinate descent, widest class first: each class tries the narrower caps
+        // with the others at their best so far (a 65-128 class has only one narrower cap that
+        // changes its tiles)
+        const int alt[3][2] = {{64, 0}, {128, 64}, {128, 64}};
+        for (int c = 2; c >= 0; --c) {
+            if (!present[c]) continue;
+            for (int a = 0; a < 2 && alt[c][a]; ++a) {
+                int caps[3] = {best_caps[0], best_caps[1], best_caps[2]};
+                caps[c] = alt[c][a];
+                qcx_status st = trial(caps);
+                if (st != QCX_OK) return st;
+            }
         }
     }
     cudaEventRecord(t1, ctx->stream);
@@ -644,9 +682,9 @@ qcx_status prepare(qcx_ctx* ctx, BatchPlan& p) {
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     p.tune_ms = tms;
-    p.tuned = ncap > 1;
-    // the kept graph reads the tile list of its own cap
-    return set_tiles(ctx, p, best_cap);
+    p.tuned = tune ? 1 : 0;
+    // the kept graph reads the tile list of its own caps
+    return set_tiles(ctx, p, best_caps);
 }
 
 }  // namespace
@@ -736,7 +774,7 @@ qcx_status qcx_solve_batch(qcx_ctx* ctx, int ninst, const int* inst_q, const dou
 qcx_status qcx_batch_info(const qcx_ctx* ctx, int n, long long* out) {
     if (!ctx || n < 1 || !out) return QCX_ERR_ARG;
     const BatchPlan* p = ctx->batch;
-    long long v[10] = {0};
+    long long v[13] = {0};
     if (p) {
         v[0] = p->tile_cap;
         v[1] = p->ntile;
@@ -748,8 +786,9 @@ qcx_status qcx_batch_info(const qcx_ctx* ctx, int n, long long* out) {
         v[7] = p->nmax;
         v[8] = (long long)(p->tune_ms * 1000.0);
         v[9] = p->prec;
+        for (int c = 0; c < 3; ++c) v[10 + c] = p->caps[c];
     }
-    for (int i = 0; i < n; ++i) out[i] = i < 10 ? v[i] : 0;
+    for (int i = 0; i < n; ++i) out[i] = i < 13 ? v[i] : 0;
     return p ? QCX_OK : QCX_ERR_STATE;
 }
 

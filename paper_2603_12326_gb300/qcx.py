@@ -400,10 +400,10 @@ class Context:
 
     def batch_info(self):
         """Facts about the current batch plan (see qcx_batch_info)."""
-        out = (ct.c_longlong * 10)()
-        self._check(qcx_batch_info(self.h, 10, out))
+        out = (ct.c_longlong * 13)()
+        self._check(qcx_batch_info(self.h, 13, out))
         keys = ["tile_cap", "tiles", "tc_ctas", "solve_ctas", "kernels_per_replay", "autotuned", "distinct_q",
-                "max_ng", "autotune_us", "precision"]
+                "max_ng", "autotune_us", "precision", "cap_ng65_128", "cap_ng129_192", "cap_ng193_up"]
         return dict(zip(keys, list(out)))
 
     def batch_autotune(self, enable: bool):

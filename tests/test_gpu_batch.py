@@ -68,6 +68,11 @@ def test_uneven_batch_matches_oracle(ctx, uneven, prec, tol):
     info = ctx.batch_info()
     assert info["distinct_q"] == p.nq and info["max_ng"] == 339
     assert info["autotuned"] == (1 if prec == QCX_MIXED else 0)
+    if prec == QCX_MIXED:
+        # one tile-width cap per N_G class, each one of the widths the autotuner tries
+        caps = (info["cap_ng65_128"], info["cap_ng129_192"], info["cap_ng193_up"])
+        assert caps[0] in (64, 192) and caps[1] in (64, 128, 192) and caps[2] in (64, 128, 192), caps
+        assert info["tile_cap"] == caps[2]
 
 
 def test_mixed_batch_matches_fp64_batch_on_all_instances(ctx, uneven):
