@@ -435,3 +435,23 @@ def test_short_ring_is_caught():
     two) lets an issuer's wait on an A-tile barrier pass one phase early."""
     bad = sum(bool(_run(20, 2, 5, seed, ngroups=1)[0]) for seed in range(20))
     assert bad > 0
+
+
+def test_warpgroup_register_budgets_fit_the_launch():
+    """k_chi0_tc trades registers between its warpgroups with setmaxnreg: one control warpgroup, two
+    A-generation and two drain warpgroups.  An increase waits until other warpgroups give registers
+    back, so the budgets must sum to at most the block's launch allocation (threads x registers per
+    thread at launch, 65536 / 640 rounded down to 8), or the drain warps would wait forever; the host
+    refuses to launch a build whose register count differs from LAUNCH_REGS."""
+    src = _src("chi0_tc.cu")
+    m = re.search(r"constexpr int REG_CTRL = (\d+), REG_AGEN = (\d+), REG_DRAIN = (\d+);", src)
+    assert m
+    ctrl, agen, drain = (int(x) for x in m.groups())
+    nthreads, launch = _constant("NTHREADS", "chi0_tc.cu"), _constant("LAUNCH_REGS", "chi0_tc.cu")
+    assert launch == (65536 // nthreads) // 8 * 8
+    assert 128 * ctrl + 256 * agen + 256 * drain <= nthreads * launch
+    for r in (ctrl, agen, drain):
+        assert r % 8 == 0 and 24 <= r <= 256          # setmaxnreg's range and granule
+    assert "if (fa.numRegs != LAUNCH_REGS) return cudaErrorNotSupported;" in src
+    # every warp of a warpgroup takes the same budget: the roles split at warpgroup boundaries
+    assert _constant("AGEN_WARP0", "chi0_tc.cu") % 4 == 0 and _constant("DRAIN_WARP0", "chi0_tc.cu") % 4 == 0
