@@ -397,7 +397,7 @@ def run_ours(args, ws, rank, local):
                "data": "synthetic (seeded states shaped like the paper's workloads)",
                "config": _config(ws, "chi0 as split-BF16 tcgen05 products: rho~ (two BF16 terms of the FP32 "
                                      "pair densities) against W rho~ in three terms, five products, FP32 "
-                                     "accumulation restarted every 40 MMAs and FP64 partial sums, diagonal summed "
+                                     "accumulation restarted every 20 MMAs and FP64 partial sums, diagonal summed "
                                      "again in FP32; inverse FP32 + FP64 diagonal correction; rate FP64", nq * nw),
                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak,

@@ -61,7 +61,7 @@ typedef enum {
     QCX_MIXED = 1   /* FP32 pair densities kept as three BF16 terms; chi0 on the tcgen05
                        tensor cores with rho~ = the first two terms on one side and W rho~
                        in three BF16 terms on the other (five products), the FP32
-                       tensor-core sums restarted every 40 MMAs and accumulated in FP64, the
+                       tensor-core sums restarted every 20 MMAs and accumulated in FP64, the
                        diagonal summed again from the three-term rho in FP32; eps stored in FP64;
                        FP32 Gauss-Jordan inverse with an FP64 residual correction of the diagonal
                        for ill-conditioned blocks (kappa_1 above qcx_set_refine_threshold, 1e4
