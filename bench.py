@@ -306,6 +306,9 @@ def run_ours(args, ws, rank, local):
         t = torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()
         pin[name] = t
     outL = torch.empty((nq, 2, nw, ng), dtype=torch.float64).pin_memory()
+    # each q's loss tables go to device memory (no per-q synchronisation: a host destination makes the
+    # library wait for the stream) and all q come back to the pinned host buffer in one copy per step
+    outL_dev = torch.empty((nq, 2, nw, ng), dtype=torch.float64, device=f"cuda:{local}")
     h2d = sum(t.numel() * t.element_size() for t in pin.values())
     d2h = outL.numel() * outL.element_size() + 2 * 10 * 8
 
@@ -318,7 +321,9 @@ def run_ours(args, ws, rank, local):
             ctx.pair_density(iq, G, QCX_MIXED)
             ctx.chi0(iq, w, eta, QCX_MIXED)
             ctx.invert_eps(iq, QCX_MIXED, want=False)
-            ctx.loss_function(iq, QCX_MIXED, out_lfe=outL[iq, 0].numpy(), out_nolfe=outL[iq, 1].numpy())
+            ctx.loss_function(iq, QCX_MIXED, out_lfe=outL_dev[iq, 0], out_nolfe=outL_dev[iq, 1])
+        with torch.cuda.stream(stream):
+            outL.copy_(outL_dev, non_blocking=True)
         Lb, cnt = ctx.bin_loss(list(range(nq)), 0, edges, nw)
         if ws > 1:
             Lb, cnt = shards.combine_bins(Lb, cnt, device=f"cuda:{local}")
